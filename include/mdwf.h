@@ -1,0 +1,169 @@
+/*
+ * libmdwf — even-odd preconditioned Moebius domain-wall fermion solves on one
+ * GB300 GPU (sm_103a).
+ *
+ * The method is the valence-quark solve of arXiv:1701.07559: the Moebius
+ * domain-wall operator (Sec. II, kernel (b5+c5) D_W / (2 + (b5-c5) D_W) with
+ * domain-wall height M5), applied on gradient-flowed SU(3) links (Sec. III),
+ * inverted through the asymmetric even-odd Schur complement (Sec. VII) by a
+ * mixed-precision conjugate-gradient solver on the normal equations (Sec. VII,
+ * "double-half mixed precision").
+ *
+ * Operators (DeGrand-Rossi gamma basis, gamma_5 = diag(1,1,-1,-1); periodic in
+ * x, y, z; antiperiodic in t unless turned off in mdwf_load_gauge):
+ *   H psi(x)  = sum_mu (1 - g_mu) U_mu(x) psi(x+mu) + (1 + g_mu) U_mu(x-mu)^+ psi(x-mu)
+ *   D_W       = (4 - M5) - H / 2
+ *   (P psi)_s = P_- psi_{s+1} + P_+ psi_{s-1},  psi_{L5} = -m_f psi_0,  psi_{-1} = -m_f psi_{L5-1}
+ *   D         = D_W (b5 + c5 P) + (1 - P)          (5D Moebius operator)
+ *   Mhat      = A_ee - D_eo A_oo^-1 D_oe,  A = (b5 d + 1) + (c5 d - 1) P,  d = 4 - M5,
+ *               D_eo = -1/2 H_eo (b5 + c5 P)
+ *
+ * Host layouts (FP64, complex interleaved re, im; x fastest):
+ *   gauge   U[t][z][y][x][mu][a][b]            mu = 0..3 for x, y, z, t
+ *   4D      psi[t][z][y][x][spin][colour]
+ *   5D      psi[s][t][z][y][x][spin][colour]   s = 0..L5-1
+ *
+ * Ownership: the caller owns every buffer passed in; the library copies what
+ * it needs (gauge fields are copied to the device at load time) and never
+ * frees caller memory.  `_dev` variants take device pointers in the same
+ * layouts plus a cudaStream_t (as void*; NULL = the context's own stream) and
+ * run asynchronously on that stream, except where noted.
+ *
+ * Errors: every call returns MDWF_OK (0) or a negative MDWF_ERR_* code;
+ * mdwf_last_error(ctx) returns a message for the last failure on ctx.
+ * A context is used by one host thread at a time.
+ */
+#ifndef MDWF_H
+#define MDWF_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MDWF_OK 0
+#define MDWF_ERR_ARG (-1)           /* invalid argument (sizes, ids, null pointers) */
+#define MDWF_ERR_NOMEM (-2)         /* device allocation failed */
+#define MDWF_ERR_NONFINITE (-3)     /* NaN or Inf in an input */
+#define MDWF_ERR_NOT_CONVERGED (-4) /* max_iter reached; outputs hold the best iterate, stats filled */
+#define MDWF_ERR_TIMEOUT (-5)       /* a bounded device wait ran out */
+#define MDWF_ERR_CUDA (-6)          /* a CUDA runtime call failed */
+#define MDWF_ERR_STATE (-7)         /* gauge field or action not set for this cfg_id */
+
+/* Storage precision of the inner (sloppy) solver vectors.  Arithmetic is FP64
+ * for MDWF_PREC_DOUBLE and FP32 otherwise; the solution accumulator, the
+ * reliable-update residuals and all global sums are FP64 in every mode. */
+#define MDWF_PREC_DOUBLE 0
+#define MDWF_PREC_SINGLE 1
+#define MDWF_PREC_HALF 2 /* fp16 with one float scale per (site, slice, RHS) */
+#define MDWF_PREC_BF16 3
+
+typedef struct mdwf_ctx mdwf_ctx;
+
+typedef struct {
+  int precision;   /* MDWF_PREC_* (default MDWF_PREC_HALF) */
+  int max_iter;    /* CG iterations per RHS (default 100000) */
+  double delta;    /* reliable update when |r| < delta * max |r| since the last one (default 0.1) */
+  int chunk;       /* CG iterations per device launch sequence between host checks (default 16) */
+  int use_graph;   /* capture each chunk in a CUDA graph (default 1) */
+  int nsb;         /* half-lattice sites per thread block tile (default 2; 0 = default) */
+  int reserved[6];
+} mdwf_solver_opts;
+
+typedef struct {
+  int iters;             /* CG iterations */
+  int reliable_updates;  /* FP64 residual recomputations (including the final check) */
+  int converged;         /* 1 if rel_true_resid <= tol */
+  int reserved0;
+  double rel_true_resid; /* ||b - D x|| / ||b|| of the returned x, in FP64 on the full lattice */
+  double time_s;         /* wall time of the call */
+} mdwf_solve_stats;
+
+/* Fill opts with the defaults listed above. */
+void mdwf_default_opts(mdwf_solver_opts* opts);
+
+/* Create a context for lattice dims = {Lx, Ly, Lz, Lt} (each even, >= 2) on CUDA
+ * device `device`.  *out receives the context.  Errors: ARG, CUDA, NOMEM. */
+int mdwf_create(const int dims[4], int device, mdwf_ctx** out);
+
+/* Release all device memory of ctx and the context itself.  NULL is accepted. */
+int mdwf_destroy(mdwf_ctx* ctx);
+
+/* Message of the last error on ctx (never NULL; empty when none). */
+const char* mdwf_last_error(const mdwf_ctx* ctx);
+
+/* Copy a gauge field (host, layout above, 18 * 4 * V doubles) into gauge slot
+ * cfg_id (>= 0) of ctx, replacing any previous field there.  t_antiperiodic = 1
+ * gives the fermion a -1 on hops across the time boundary (the convention of
+ * the paper's ensembles), 0 makes time periodic.  Errors: ARG, NONFINITE, NOMEM, CUDA. */
+int mdwf_load_gauge(mdwf_ctx* ctx, int cfg_id, const double* U, int t_antiperiodic);
+
+/* Set the Moebius action of cfg_id: domain-wall height M5, Moebius b5, c5
+ * (Sec. II), quark mass m_f, fifth-dimension extent L5 (2..32).  The paper's
+ * tuned values are in its Table II.  Errors: ARG. */
+int mdwf_set_action(mdwf_ctx* ctx, int cfg_id, double M5, double b5, double c5, double mf, int L5);
+
+/* Hopping term on all L5 slices, out = H in (dagger = 0) or H^+ in (dagger = 1),
+ * in FP64.  out_parity = 0 or 1 writes the sites of that parity (reading the
+ * other parity of `in`) and zeroes the rest of out; -1 writes every site.
+ * in, out: host 5D fields of L5 * V * 24 doubles.  Errors: ARG, STATE, NONFINITE, CUDA. */
+int mdwf_apply_dslash(mdwf_ctx* ctx, int cfg_id, const double* in, double* out, int out_parity, int dagger);
+
+/* The 5D Moebius operator on the full lattice in FP64: out = D in (dagger = 0)
+ * or D^+ in (dagger = 1).  Host 5D fields.  Errors: ARG, STATE, NONFINITE, CUDA. */
+int mdwf_apply_mdwf(mdwf_ctx* ctx, int cfg_id, const double* in, double* out, int dagger);
+
+/* The asymmetric Schur operator on even sites (Sec. VII): out_e = Mhat in_e
+ * (dagger = 0) or Mhat^+ in_e.  Host 5D full-lattice fields; odd sites of in are
+ * ignored and odd sites of out are set to zero.  precision = MDWF_PREC_* selects
+ * the storage/arithmetic of the kernels that run (FP64 for MDWF_PREC_DOUBLE).
+ * Errors: ARG, STATE, NONFINITE, CUDA. */
+int mdwf_apply_schur(mdwf_ctx* ctx, int cfg_id, const double* in, double* out, int dagger, int precision);
+
+/* A fifth-dimension operator on the full lattice in FP64: op = 0 for
+ * A = (b5 d + 1) + (c5 d - 1) P, 1 for B = b5 + c5 P, 2 for A^-1 (closed form);
+ * dagger = 1 for the adjoint.  Host 5D fields.  Errors: ARG, STATE, CUDA. */
+int mdwf_apply_5d(mdwf_ctx* ctx, int cfg_id, int op, const double* in, double* out, int dagger);
+
+/* 5D source from a 4D field eta (host, V * 24 doubles):
+ * src = (1 - c5 D_W) (P_+ eta delta_{s,0} + P_- eta delta_{s,L5-1}), the wall
+ * injection under which q = P_- x_0 + P_+ x_{L5-1} (mdwf_extract_prop4d) is the
+ * 4D quark propagator of the Moebius kernel.  Errors: ARG, STATE, NONFINITE, CUDA. */
+int mdwf_make_source(mdwf_ctx* ctx, int cfg_id, const double* eta4d, double* src5d);
+
+/* Solve D x = src for one host 5D source to ||src - D x|| / ||src|| <= tol,
+ * through the even-odd Schur complement with CG on the normal equations and
+ * reliable updates in FP64.  x5d (host) receives x.  opts may be NULL
+ * (defaults); stats may be NULL.  Errors: ARG, STATE, NONFINITE, NOMEM, CUDA,
+ * NOT_CONVERGED (x5d holds the last iterate). */
+int mdwf_solve(mdwf_ctx* ctx, int cfg_id, const double* src5d, double* x5d, double tol,
+               const mdwf_solver_opts* opts, mdwf_solve_stats* stats);
+
+/* Solve n systems in one batched launch sequence: D(m_i) x_i = srcs[i], the
+ * action of cfg_id with the quark mass replaced by masses[i] (masses may be NULL
+ * for the action's m_f).  srcs[i], xs[i]: host 5D fields; stats: n entries or
+ * NULL.  All right-hand sides share every kernel launch; each keeps its own CG
+ * scalars and stops on its own.  Errors as mdwf_solve (NOT_CONVERGED if any
+ * system did not converge). */
+int mdwf_solve_batch(mdwf_ctx* ctx, int cfg_id, int n, const double* const* srcs, const double* masses,
+                     double* const* xs, double tol, const mdwf_solver_opts* opts, mdwf_solve_stats* stats);
+
+/* As mdwf_solve_batch with device pointers (layout above) on `stream`.  The
+ * call returns when the solves are finished (it reads convergence flags back
+ * between chunks).  Errors as mdwf_solve_batch. */
+int mdwf_solve_batch_dev(mdwf_ctx* ctx, int cfg_id, int n, const double* const* srcs, const double* masses,
+                         double* const* xs, double tol, const mdwf_solver_opts* opts, mdwf_solve_stats* stats,
+                         void* stream);
+
+/* Device-pointer variants of the operator applies, on `stream` (asynchronous). */
+int mdwf_apply_dslash_dev(mdwf_ctx* ctx, int cfg_id, const double* in, double* out, int out_parity, int dagger,
+                          void* stream);
+int mdwf_apply_mdwf_dev(mdwf_ctx* ctx, int cfg_id, const double* in, double* out, int dagger, void* stream);
+
+/* 4D propagator from a 5D solution: q = P_- x_0 + P_+ x_{L5-1} (host arrays;
+ * x5d has L5 * V * 24 doubles, q4d V * 24).  Pure host code.  Errors: ARG. */
+int mdwf_extract_prop4d(const double* x5d, const int dims[4], int L5, double* q4d);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MDWF_H */

@@ -1,0 +1,287 @@
+// Vector kernels of the solver: layout conversion, precision conversion,
+// the CG updates with their fused norms, and the fixed-order reductions.
+//
+// All unit-wise kernels use the tile mapping of the hop kernel (tile of nsb
+// sites x L5 slices x rt slots per block), so per-slot partial sums are formed
+// per tile in a fixed order and the final sum over tiles is also fixed: a
+// slot's result does not depend on how many other slots share the launch.
+#include "blas.h"
+
+namespace mdwf {
+
+struct Unit {
+  long h;
+  int s, r, site_l, r_l;
+  bool valid;
+  long u;
+};
+
+__device__ __forceinline__ Unit unit_of(const Tiling& tl, long Vh, int L5, int N) {
+  Unit x;
+  const int tid = threadIdx.x;
+  x.r_l = tid % tl.rt;
+  x.s = (tid / tl.rt) % L5;
+  x.site_l = tid / (tl.rt * L5);
+  x.h = (long)blockIdx.x * tl.nsb + x.site_l;
+  x.r = blockIdx.y * tl.rt + x.r_l;
+  x.valid = (x.h < Vh) && (x.r < N);
+  x.u = (x.h * L5 + x.s) * N + x.r;
+  return x;
+}
+
+// Per-slot sum of `v` over the block's (site, s) units, written to partials[tile][r].
+__device__ __forceinline__ void block_partial(double v, const Unit& x, const Tiling& tl, int L5, int N,
+                                              double* __restrict__ partials) {
+  __shared__ double sred[1024];
+  sred[threadIdx.x] = v;
+  __syncthreads();
+  if (x.s == 0 && x.site_l == 0 && x.r < N) {
+    double sum = 0.0;
+    for (int k = 0; k < tl.nsb * L5; k++) sum += sred[k * tl.rt + x.r_l];
+    partials[(long)blockIdx.x * N + x.r] = sum;
+  }
+}
+
+template <typename S>
+__global__ void k_pack(const double* __restrict__ api, S* __restrict__ out, float* __restrict__ out_nrm, Geom g,
+                       int L5, int N, int par, int r) {
+  using T = typename StoreTraits<S>::T;
+  long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= g.Vh * L5) return;
+  long h = idx / L5;
+  int s = (int)(idx - h * L5);
+  int c[4];
+  site_coords(g, par, h, c);
+  long lex = lex_index(g, c);
+  const double* src = api + ((long)s * g.V + lex) * 24;
+  T a[24];
+#pragma unroll
+  for (int i = 0; i < 24; i++) a[i] = (T)src[i];
+  store24<S, T>(out, out_nrm, (h * L5 + s) * N + r, a);
+}
+
+template <typename S>
+__global__ void k_unpack(const S* __restrict__ in, const float* __restrict__ in_nrm, double* __restrict__ api, Geom g,
+                         int L5, int N, int par, int r) {
+  using T = typename StoreTraits<S>::T;
+  long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= g.Vh * L5) return;
+  long h = idx / L5;
+  int s = (int)(idx - h * L5);
+  int c[4];
+  site_coords(g, par, h, c);
+  long lex = lex_index(g, c);
+  double* dst = api + ((long)s * g.V + lex) * 24;
+  T a[24];
+  load24<S, T>(in, in_nrm, (h * L5 + s) * N + r, a);
+#pragma unroll
+  for (int i = 0; i < 24; i++) dst[i] = (double)a[i];
+}
+
+template <typename Si, typename So>
+__global__ void k_convert(const Si* __restrict__ in, const float* __restrict__ in_nrm, So* __restrict__ out,
+                          float* __restrict__ out_nrm, Tiling tl, long Vh, int L5, int N, const int* __restrict__ mask) {
+  Unit x = unit_of(tl, Vh, L5, N);
+  if (!x.valid || (mask && !mask[x.r])) return;
+  using Ti = typename StoreTraits<Si>::T;
+  using To = typename StoreTraits<So>::T;
+  Ti a[24];
+  load24<Si, Ti>(in, in_nrm, x.u, a);
+  To b[24];
+#pragma unroll
+  for (int i = 0; i < 24; i++) b[i] = (To)a[i];
+  store24<So, To>(out, out_nrm, x.u, b);
+}
+
+// x += alpha_r p ; rho -= alpha_r q ; partial |rho|^2
+template <typename SX, typename S>
+__global__ void k_axpy_x_rho(SX* __restrict__ xv, const S* __restrict__ p, const float* __restrict__ p_nrm,
+                             S* __restrict__ rho, float* __restrict__ rho_nrm, const S* __restrict__ q,
+                             const float* __restrict__ q_nrm, const double* __restrict__ alpha, Tiling tl, long Vh,
+                             int L5, int N, const int* __restrict__ active, double* __restrict__ partials) {
+  using T = typename StoreTraits<S>::T;
+  using TX = typename StoreTraits<SX>::T;
+  Unit x = unit_of(tl, Vh, L5, N);
+  double n2 = 0.0;
+  if (x.valid && (!active || active[x.r])) {
+    const T a = (T)alpha[x.r];
+    T pv[24], qv[24], rv[24];
+    TX xv_[24];
+    load24<S, T>(p, p_nrm, x.u, pv);
+    load24<S, T>(q, q_nrm, x.u, qv);
+    load24<S, T>(rho, rho_nrm, x.u, rv);
+    load24<SX, TX>(xv, nullptr, x.u, xv_);
+#pragma unroll
+    for (int i = 0; i < 24; i++) {
+      xv_[i] += (TX)(a * pv[i]);
+      rv[i] -= a * qv[i];
+      n2 += (double)rv[i] * (double)rv[i];
+    }
+    store24<SX, TX>(xv, nullptr, x.u, xv_);
+    store24<S, T>(rho, rho_nrm, x.u, rv);
+  }
+  block_partial(n2, x, tl, L5, N, partials);
+}
+
+// p = r + beta_r p
+template <typename S>
+__global__ void k_xpay(const S* __restrict__ r, const float* __restrict__ r_nrm, S* __restrict__ p,
+                       float* __restrict__ p_nrm, const double* __restrict__ beta, Tiling tl, long Vh, int L5, int N,
+                       const int* __restrict__ active) {
+  using T = typename StoreTraits<S>::T;
+  Unit x = unit_of(tl, Vh, L5, N);
+  if (!x.valid || (active && !active[x.r])) return;
+  const T b = (T)beta[x.r];
+  T rv[24], pv[24];
+  load24<S, T>(r, r_nrm, x.u, rv);
+  load24<S, T>(p, p_nrm, x.u, pv);
+#pragma unroll
+  for (int i = 0; i < 24; i++) pv[i] = rv[i] + b * pv[i];
+  store24<S, T>(p, p_nrm, x.u, pv);
+}
+
+// xhi += xlo ; xlo = 0
+template <typename SX>
+__global__ void k_accum_xhi(double* __restrict__ xhi, SX* __restrict__ xlo, Tiling tl, long Vh, int L5, int N,
+                            const int* __restrict__ mask) {
+  using TX = typename StoreTraits<SX>::T;
+  Unit x = unit_of(tl, Vh, L5, N);
+  if (!x.valid || (mask && !mask[x.r])) return;
+  double h[24];
+  TX l[24];
+  load24<double, double>(xhi, nullptr, x.u, h);
+  load24<SX, TX>(xlo, nullptr, x.u, l);
+#pragma unroll
+  for (int i = 0; i < 24; i++) { h[i] += (double)l[i]; l[i] = 0; }
+  store24<double, double>(xhi, nullptr, x.u, h);
+  store24<SX, TX>(xlo, nullptr, x.u, l);
+}
+
+template <typename S>
+__global__ void k_norm2(const S* __restrict__ v, const float* __restrict__ v_nrm, Tiling tl, long Vh, int L5, int N,
+                        const int* __restrict__ mask, double* __restrict__ partials) {
+  using T = typename StoreTraits<S>::T;
+  Unit x = unit_of(tl, Vh, L5, N);
+  double n2 = 0.0;
+  if (x.valid && (!mask || mask[x.r])) {
+    T a[24];
+    load24<S, T>(v, v_nrm, x.u, a);
+#pragma unroll
+    for (int i = 0; i < 24; i++) n2 += (double)a[i] * (double)a[i];
+  }
+  block_partial(n2, x, tl, L5, N, partials);
+}
+
+// out[r] = sum_tiles partials[tile][r], fixed order: thread t takes tiles t, t+T, ..., then a fixed tree.
+__global__ void k_finalize(const double* __restrict__ partials, long ntiles, int N, double* __restrict__ out) {
+  __shared__ double sh[256];
+  const int r = blockIdx.x;
+  double s = 0.0;
+  for (long k = threadIdx.x; k < ntiles; k += blockDim.x) s += partials[k * N + r];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[r] = sh[0];
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+static inline dim3 tile_grid(const Tiling& t) { return dim3((unsigned)t.ntiles, (unsigned)t.ngroups); }
+
+template <typename S>
+cudaError_t pack_rhs(const double* api, S* out, float* out_nrm, const Geom& g, int L5, int N, int par, int r,
+                     cudaStream_t st) {
+  long n = g.Vh * L5;
+  k_pack<S><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(api, out, out_nrm, g, L5, N, par, r);
+  return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t unpack_rhs(const S* in, const float* in_nrm, double* api, const Geom& g, int L5, int N, int par, int r,
+                       cudaStream_t st) {
+  long n = g.Vh * L5;
+  k_unpack<S><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(in, in_nrm, api, g, L5, N, par, r);
+  return cudaGetLastError();
+}
+
+template <typename Si, typename So>
+cudaError_t convert(const Si* in, const float* in_nrm, So* out, float* out_nrm, const Tiling& t, long Vh, int L5,
+                    int N, const int* mask, cudaStream_t st) {
+  k_convert<Si, So><<<tile_grid(t), t.threads, 0, st>>>(in, in_nrm, out, out_nrm, t, Vh, L5, N, mask);
+  return cudaGetLastError();
+}
+
+template <typename SX, typename S>
+cudaError_t axpy_x_rho(SX* x, const S* p, const float* p_nrm, S* rho, float* rho_nrm, const S* q, const float* q_nrm,
+                       const double* alpha, const Tiling& t, long Vh, int L5, int N, const int* active,
+                       double* partials, cudaStream_t st) {
+  k_axpy_x_rho<SX, S><<<tile_grid(t), t.threads, 0, st>>>(x, p, p_nrm, rho, rho_nrm, q, q_nrm, alpha, t, Vh, L5, N,
+                                                           active, partials);
+  return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t xpay(const S* r, const float* r_nrm, S* p, float* p_nrm, const double* beta, const Tiling& t, long Vh,
+                 int L5, int N, const int* active, cudaStream_t st) {
+  k_xpay<S><<<tile_grid(t), t.threads, 0, st>>>(r, r_nrm, p, p_nrm, beta, t, Vh, L5, N, active);
+  return cudaGetLastError();
+}
+
+template <typename SX>
+cudaError_t accum_xhi(double* xhi, SX* xlo, const Tiling& t, long Vh, int L5, int N, const int* mask,
+                      cudaStream_t st) {
+  k_accum_xhi<SX><<<tile_grid(t), t.threads, 0, st>>>(xhi, xlo, t, Vh, L5, N, mask);
+  return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t norm2_partials(const S* v, const float* v_nrm, const Tiling& t, long Vh, int L5, int N, const int* mask,
+                           double* partials, cudaStream_t st) {
+  k_norm2<S><<<tile_grid(t), t.threads, 0, st>>>(v, v_nrm, t, Vh, L5, N, mask, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t finalize(const double* partials, long ntiles, int N, double* out, cudaStream_t st) {
+  k_finalize<<<N, 256, 0, st>>>(partials, ntiles, N, out);
+  return cudaGetLastError();
+}
+
+#define MDWF_INST_S(S)                                                                                          \
+  template cudaError_t pack_rhs<S>(const double*, S*, float*, const Geom&, int, int, int, int, cudaStream_t);   \
+  template cudaError_t unpack_rhs<S>(const S*, const float*, double*, const Geom&, int, int, int, int,          \
+                                     cudaStream_t);                                                             \
+  template cudaError_t xpay<S>(const S*, const float*, S*, float*, const double*, const Tiling&, long, int, int, \
+                               const int*, cudaStream_t);                                                       \
+  template cudaError_t norm2_partials<S>(const S*, const float*, const Tiling&, long, int, int, const int*,      \
+                                         double*, cudaStream_t);
+
+MDWF_INST_S(double)
+MDWF_INST_S(float)
+MDWF_INST_S(__half)
+MDWF_INST_S(__nv_bfloat16)
+
+#define MDWF_INST_CONV(A, B)                                                                                  \
+  template cudaError_t convert<A, B>(const A*, const float*, B*, float*, const Tiling&, long, int, int,       \
+                                     const int*, cudaStream_t);
+MDWF_INST_CONV(double, float)
+MDWF_INST_CONV(double, __half)
+MDWF_INST_CONV(double, __nv_bfloat16)
+MDWF_INST_CONV(double, double)
+
+#define MDWF_INST_AXPY(SX, S)                                                                                    \
+  template cudaError_t axpy_x_rho<SX, S>(SX*, const S*, const float*, S*, float*, const S*, const float*,        \
+                                         const double*, const Tiling&, long, int, int, const int*, double*,      \
+                                         cudaStream_t);
+MDWF_INST_AXPY(double, double)
+MDWF_INST_AXPY(float, float)
+MDWF_INST_AXPY(float, __half)
+MDWF_INST_AXPY(float, __nv_bfloat16)
+
+template cudaError_t accum_xhi<double>(double*, double*, const Tiling&, long, int, int, const int*, cudaStream_t);
+template cudaError_t accum_xhi<float>(double*, float*, const Tiling&, long, int, int, const int*, cudaStream_t);
+
+}  // namespace mdwf

@@ -1,0 +1,38 @@
+// Declarations of the vector kernels in blas.cu.
+#pragma once
+#include "mdwf_internal.h"
+
+namespace mdwf {
+
+// API layout (one RHS, [s][t][z][y][x][spin][colour][re,im], FP64, device) <-> slot r of a parity field.
+template <typename S>
+cudaError_t pack_rhs(const double* api, S* out, float* out_nrm, const Geom& g, int L5, int N, int par, int r,
+                     cudaStream_t st);
+template <typename S>
+cudaError_t unpack_rhs(const S* in, const float* in_nrm, double* api, const Geom& g, int L5, int N, int par, int r,
+                       cudaStream_t st);
+
+template <typename Si, typename So>
+cudaError_t convert(const Si* in, const float* in_nrm, So* out, float* out_nrm, const Tiling& t, long Vh, int L5,
+                    int N, const int* mask, cudaStream_t st);
+
+template <typename SX, typename S>
+cudaError_t axpy_x_rho(SX* x, const S* p, const float* p_nrm, S* rho, float* rho_nrm, const S* q, const float* q_nrm,
+                       const double* alpha, const Tiling& t, long Vh, int L5, int N, const int* active,
+                       double* partials, cudaStream_t st);
+
+template <typename S>
+cudaError_t xpay(const S* r, const float* r_nrm, S* p, float* p_nrm, const double* beta, const Tiling& t, long Vh,
+                 int L5, int N, const int* active, cudaStream_t st);
+
+template <typename SX>
+cudaError_t accum_xhi(double* xhi, SX* xlo, const Tiling& t, long Vh, int L5, int N, const int* mask,
+                      cudaStream_t st);
+
+template <typename S>
+cudaError_t norm2_partials(const S* v, const float* v_nrm, const Tiling& t, long Vh, int L5, int N, const int* mask,
+                           double* partials, cudaStream_t st);
+
+cudaError_t finalize(const double* partials, long ntiles, int N, double* out, cudaStream_t st);
+
+}  // namespace mdwf

@@ -1,0 +1,310 @@
+"""Thin ctypes binding of libmdwf (include/mdwf.h), same function names.
+
+Argument marshalling only: every operator and solver step runs in the CUDA
+library.  There is no CPU fallback; if libmdwf.so has not been built the
+import of this module fails.
+
+Host fields are numpy complex128 arrays in the C ABI's layouts:
+  gauge  [t, z, y, x, mu, 3, 3]      4D spinor [t, z, y, x, spin, colour]
+  5D spinor [s, t, z, y, x, spin, colour]
+Device fields (``*_dev`` functions) are torch CUDA tensors of the same shapes,
+dtype complex128 (or float64 with a trailing axis of 2).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, 'libmdwf.so')
+if not os.path.exists(_LIB_PATH):
+    raise ImportError('libmdwf.so is not built; run paper_1701_07559_gb300.build.build() '
+                      '(or __graft_entry__.build()) first')
+_lib = ctypes.CDLL(_LIB_PATH)
+
+MDWF_OK = 0
+MDWF_ERR_ARG = -1
+MDWF_ERR_NOMEM = -2
+MDWF_ERR_NONFINITE = -3
+MDWF_ERR_NOT_CONVERGED = -4
+MDWF_ERR_TIMEOUT = -5
+MDWF_ERR_CUDA = -6
+MDWF_ERR_STATE = -7
+
+MDWF_PREC_DOUBLE = 0
+MDWF_PREC_SINGLE = 1
+MDWF_PREC_HALF = 2
+MDWF_PREC_BF16 = 3
+PRECISIONS = {'double': 0, 'single': 1, 'half': 2, 'bf16': 3}
+
+_ERRNAMES = {v: k for k, v in globals().items() if k.startswith('MDWF_ERR_')}
+
+
+class mdwf_solver_opts(ctypes.Structure):
+    _fields_ = [('precision', ctypes.c_int), ('max_iter', ctypes.c_int), ('delta', ctypes.c_double),
+                ('chunk', ctypes.c_int), ('use_graph', ctypes.c_int), ('nsb', ctypes.c_int),
+                ('reserved', ctypes.c_int * 6)]
+
+
+class mdwf_solve_stats(ctypes.Structure):
+    _fields_ = [('iters', ctypes.c_int), ('reliable_updates', ctypes.c_int), ('converged', ctypes.c_int),
+                ('reserved0', ctypes.c_int), ('rel_true_resid', ctypes.c_double), ('time_s', ctypes.c_double)]
+
+    def as_dict(self):
+        return {'iters': self.iters, 'reliable_updates': self.reliable_updates, 'converged': bool(self.converged),
+                'rel_true_resid': self.rel_true_resid, 'time_s': self.time_s}
+
+
+class MdwfError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__('%s (%d): %s' % (_ERRNAMES.get(code, 'MDWF_ERR'), code, msg))
+        self.code = code
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_sig = {
+    'mdwf_default_opts': (None, [ctypes.POINTER(mdwf_solver_opts)]),
+    'mdwf_create': (_I, [ctypes.POINTER(_I), _I, ctypes.POINTER(_P)]),
+    'mdwf_destroy': (_I, [_P]),
+    'mdwf_last_error': (ctypes.c_char_p, [_P]),
+    'mdwf_load_gauge': (_I, [_P, _I, _P, _I]),
+    'mdwf_set_action': (_I, [_P, _I, _D, _D, _D, _D, _I]),
+    'mdwf_apply_dslash': (_I, [_P, _I, _P, _P, _I, _I]),
+    'mdwf_apply_mdwf': (_I, [_P, _I, _P, _P, _I]),
+    'mdwf_apply_schur': (_I, [_P, _I, _P, _P, _I, _I]),
+    'mdwf_apply_5d': (_I, [_P, _I, _I, _P, _P, _I]),
+    'mdwf_make_source': (_I, [_P, _I, _P, _P]),
+    'mdwf_solve': (_I, [_P, _I, _P, _P, _D, ctypes.POINTER(mdwf_solver_opts), ctypes.POINTER(mdwf_solve_stats)]),
+    'mdwf_solve_batch': (_I, [_P, _I, _I, ctypes.POINTER(_P), _P, ctypes.POINTER(_P), _D,
+                              ctypes.POINTER(mdwf_solver_opts), ctypes.POINTER(mdwf_solve_stats)]),
+    'mdwf_solve_batch_dev': (_I, [_P, _I, _I, ctypes.POINTER(_P), _P, ctypes.POINTER(_P), _D,
+                                  ctypes.POINTER(mdwf_solver_opts), ctypes.POINTER(mdwf_solve_stats), _P]),
+    'mdwf_apply_dslash_dev': (_I, [_P, _I, _P, _P, _I, _I, _P]),
+    'mdwf_apply_mdwf_dev': (_I, [_P, _I, _P, _P, _I, _P]),
+    'mdwf_extract_prop4d': (_I, [_P, ctypes.POINTER(_I), _I, _P]),
+}
+for _name, (_res, _args) in _sig.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+EXPORTED = tuple(_sig)
+
+
+class Context:
+    """Opaque handle of an mdwf_ctx (one lattice geometry on one device)."""
+
+    def __init__(self, handle, dims):
+        self.handle = handle
+        self.dims = tuple(int(d) for d in dims)
+        self.L5 = {}
+
+    @property
+    def V(self):
+        d = self.dims
+        return d[0] * d[1] * d[2] * d[3]
+
+
+def _check(ctx, rc):
+    if rc != MDWF_OK:
+        msg = _lib.mdwf_last_error(ctx.handle if ctx is not None else None)
+        raise MdwfError(rc, msg.decode() if msg else '')
+
+
+def _host(a, shape):
+    a = np.ascontiguousarray(a, dtype=np.complex128)
+    if a.shape != tuple(shape):
+        raise ValueError('expected shape %s, got %s' % (tuple(shape), a.shape))
+    return a
+
+
+def _shape5(ctx, cfg_id):
+    d = ctx.dims
+    if cfg_id not in ctx.L5:
+        raise MdwfError(MDWF_ERR_STATE, 'no action set for cfg_id %r' % (cfg_id,))
+    return (ctx.L5[cfg_id], d[3], d[2], d[1], d[0], 4, 3)
+
+
+def _ptr(a):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def mdwf_default_opts(**over):
+    o = mdwf_solver_opts()
+    _lib.mdwf_default_opts(ctypes.byref(o))
+    for k, v in over.items():
+        if k == 'precision' and isinstance(v, str):
+            v = PRECISIONS[v]
+        setattr(o, k, v)
+    return o
+
+
+def mdwf_create(dims, device=0):
+    d = (_I * 4)(*[int(x) for x in dims])
+    h = _P()
+    rc = _lib.mdwf_create(d, int(device), ctypes.byref(h))
+    if rc != MDWF_OK:
+        raise MdwfError(rc, 'mdwf_create failed (dims must be even and >= 2; device must exist)')
+    return Context(h, dims)
+
+
+def mdwf_destroy(ctx):
+    if ctx is not None and ctx.handle:
+        _lib.mdwf_destroy(ctx.handle)
+        ctx.handle = None
+
+
+def mdwf_last_error(ctx):
+    return _lib.mdwf_last_error(ctx.handle).decode()
+
+
+def mdwf_load_gauge(ctx, cfg_id, U, t_antiperiodic=1):
+    d = ctx.dims
+    U = _host(U, (d[3], d[2], d[1], d[0], 4, 3, 3))
+    _check(ctx, _lib.mdwf_load_gauge(ctx.handle, int(cfg_id), _ptr(U), int(t_antiperiodic)))
+
+
+def mdwf_set_action(ctx, cfg_id, M5, b5, c5, mf, L5):
+    _check(ctx, _lib.mdwf_set_action(ctx.handle, int(cfg_id), float(M5), float(b5), float(c5), float(mf), int(L5)))
+    ctx.L5[cfg_id] = int(L5)
+
+
+def mdwf_apply_dslash(ctx, cfg_id, psi, out_parity=-1, dagger=0):
+    shape = _shape5(ctx, cfg_id)
+    psi = _host(psi, shape)
+    out = np.empty(shape, dtype=np.complex128)
+    _check(ctx, _lib.mdwf_apply_dslash(ctx.handle, int(cfg_id), _ptr(psi), _ptr(out), int(out_parity), int(dagger)))
+    return out
+
+
+def mdwf_apply_mdwf(ctx, cfg_id, psi, dagger=0):
+    shape = _shape5(ctx, cfg_id)
+    psi = _host(psi, shape)
+    out = np.empty(shape, dtype=np.complex128)
+    _check(ctx, _lib.mdwf_apply_mdwf(ctx.handle, int(cfg_id), _ptr(psi), _ptr(out), int(dagger)))
+    return out
+
+
+def mdwf_apply_schur(ctx, cfg_id, psi, dagger=0, precision=MDWF_PREC_DOUBLE):
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    shape = _shape5(ctx, cfg_id)
+    psi = _host(psi, shape)
+    out = np.empty(shape, dtype=np.complex128)
+    _check(ctx, _lib.mdwf_apply_schur(ctx.handle, int(cfg_id), _ptr(psi), _ptr(out), int(dagger), int(precision)))
+    return out
+
+
+def mdwf_apply_5d(ctx, cfg_id, op, psi, dagger=0):
+    """op: 0 = A, 1 = B, 2 = A^-1 (or 'A', 'B', 'Ainv')."""
+    if isinstance(op, str):
+        op = {'A': 0, 'B': 1, 'Ainv': 2}[op]
+    shape = _shape5(ctx, cfg_id)
+    psi = _host(psi, shape)
+    out = np.empty(shape, dtype=np.complex128)
+    _check(ctx, _lib.mdwf_apply_5d(ctx.handle, int(cfg_id), int(op), _ptr(psi), _ptr(out), int(dagger)))
+    return out
+
+
+def mdwf_make_source(ctx, cfg_id, eta):
+    d = ctx.dims
+    eta = _host(eta, (d[3], d[2], d[1], d[0], 4, 3))
+    out = np.empty(_shape5(ctx, cfg_id), dtype=np.complex128)
+    _check(ctx, _lib.mdwf_make_source(ctx.handle, int(cfg_id), _ptr(eta), _ptr(out)))
+    return out
+
+
+def mdwf_solve(ctx, cfg_id, src, tol, opts=None):
+    """Returns (x, stats dict).  Raises MdwfError on failure (including not converged)."""
+    shape = _shape5(ctx, cfg_id)
+    src = _host(src, shape)
+    x = np.empty(shape, dtype=np.complex128)
+    st = mdwf_solve_stats()
+    o = opts if opts is not None else mdwf_default_opts()
+    _check(ctx, _lib.mdwf_solve(ctx.handle, int(cfg_id), _ptr(src), _ptr(x), float(tol), ctypes.byref(o),
+                                ctypes.byref(st)))
+    return x, st.as_dict()
+
+
+def mdwf_solve_batch(ctx, cfg_id, srcs, tol, masses=None, opts=None, raise_on_nonconv=True):
+    """Solve len(srcs) systems in one batch.  Returns (list of x, list of stats dicts)."""
+    shape = _shape5(ctx, cfg_id)
+    n = len(srcs)
+    hs = [_host(s, shape) for s in srcs]
+    xs = [np.empty(shape, dtype=np.complex128) for _ in range(n)]
+    sp = (_P * n)(*[s.ctypes.data for s in hs])
+    xp = (_P * n)(*[x.ctypes.data for x in xs])
+    m = None
+    if masses is not None:
+        m = np.ascontiguousarray(masses, dtype=np.float64)
+        if m.shape != (n,):
+            raise ValueError('masses must have one entry per source')
+    st = (mdwf_solve_stats * n)()
+    o = opts if opts is not None else mdwf_default_opts()
+    rc = _lib.mdwf_solve_batch(ctx.handle, int(cfg_id), n, sp, _ptr(m) if m is not None else None, xp, float(tol),
+                               ctypes.byref(o), st)
+    if rc != MDWF_OK and (raise_on_nonconv or rc != MDWF_ERR_NOT_CONVERGED):
+        _check(ctx, rc)
+    return xs, [s.as_dict() for s in st]
+
+
+def _dev_ptr(t, shape):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
+        raise ValueError('expected a contiguous CUDA tensor')
+    if t.dtype == torch.complex128:
+        ok = tuple(t.shape) == tuple(shape)
+    elif t.dtype == torch.float64:
+        ok = tuple(t.shape) == tuple(shape) + (2,)
+    else:
+        ok = False
+    if not ok:
+        raise ValueError('expected complex128 %s (or float64 with a trailing 2), got %s %s'
+                         % (tuple(shape), t.dtype, tuple(t.shape)))
+    return t.data_ptr()
+
+
+def mdwf_solve_batch_dev(ctx, cfg_id, srcs, xs, tol, masses=None, opts=None, stream=None, raise_on_nonconv=True):
+    """Batched solve on torch CUDA tensors (srcs read, xs written).  stream: torch.cuda.Stream or None."""
+    shape = _shape5(ctx, cfg_id)
+    n = len(srcs)
+    sp = (_P * n)(*[_dev_ptr(s, shape) for s in srcs])
+    xp = (_P * n)(*[_dev_ptr(x, shape) for x in xs])
+    m = None
+    if masses is not None:
+        m = np.ascontiguousarray(masses, dtype=np.float64)
+    st = (mdwf_solve_stats * n)()
+    o = opts if opts is not None else mdwf_default_opts()
+    sh = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+    rc = _lib.mdwf_solve_batch_dev(ctx.handle, int(cfg_id), n, sp, _ptr(m) if m is not None else None, xp,
+                                   float(tol), ctypes.byref(o), st, sh)
+    if rc != MDWF_OK and (raise_on_nonconv or rc != MDWF_ERR_NOT_CONVERGED):
+        _check(ctx, rc)
+    return [s.as_dict() for s in st]
+
+
+def mdwf_apply_dslash_dev(ctx, cfg_id, psi, out, out_parity=-1, dagger=0, stream=None):
+    shape = _shape5(ctx, cfg_id)
+    sh = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+    _check(ctx, _lib.mdwf_apply_dslash_dev(ctx.handle, int(cfg_id), _dev_ptr(psi, shape), _dev_ptr(out, shape),
+                                           int(out_parity), int(dagger), sh))
+
+
+def mdwf_apply_mdwf_dev(ctx, cfg_id, psi, out, dagger=0, stream=None):
+    shape = _shape5(ctx, cfg_id)
+    sh = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+    _check(ctx, _lib.mdwf_apply_mdwf_dev(ctx.handle, int(cfg_id), _dev_ptr(psi, shape), _dev_ptr(out, shape),
+                                         int(dagger), sh))
+
+
+def mdwf_extract_prop4d(x5d, dims, L5):
+    Lx, Ly, Lz, Lt = dims
+    x5d = _host(x5d, (L5, Lt, Lz, Ly, Lx, 4, 3))
+    q = np.empty((Lt, Lz, Ly, Lx, 4, 3), dtype=np.complex128)
+    d = (_I * 4)(*[int(v) for v in dims])
+    rc = _lib.mdwf_extract_prop4d(_ptr(x5d), d, int(L5), _ptr(q))
+    if rc != MDWF_OK:
+        raise MdwfError(rc, 'mdwf_extract_prop4d: bad arguments')
+    return q

@@ -1,0 +1,232 @@
+"""GPU parity: every step of the hot path, called through the C ABI, against the
+FP64 CPU oracle on the same seeded inputs.
+
+Tolerances (norm-wise relative, ||gpu - oracle|| / ||oracle||):
+  FP64 operator applies                     1e-13
+  FP32 storage/arithmetic Schur operator   2e-6   (a few float roundings per term)
+  fp16 storage (scaled), FP32 arithmetic   4e-3   (2^-11 rounding of each stored field)
+  bf16 storage, FP32 arithmetic            3e-2   (2^-8 rounding of each stored field)
+  solves: true FP64 residual ||b - D x||/||b|| <= 1e-10 recomputed by the oracle's D,
+          and the error against the oracle's own solution below kappa * 1e-10.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import mdwf_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+M = None
+
+
+def setup_module(module):
+    global M
+    from paper_1701_07559_gb300 import build
+    build.build()
+    from paper_1701_07559_gb300 import mdwf
+    M = mdwf
+
+
+def _rel(a, b):
+    return np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel())
+
+
+# (dims, L5, action, gauge seed/eps): several tiles, ragged tails (Vh*L5 not a
+# multiple of the tile), anisotropic extents and L5 from 2 to 12.
+CASES = [
+    ((4, 4, 4, 8), 4, (1.3, 1.5, 0.5, 0.1), (1, 0.3)),          # the oracle-sized workload
+    ((6, 4, 2, 4), 5, (1.2, 1.25, 0.25, 0.05), (2, 0.5)),
+    ((2, 2, 2, 2), 2, (1.1, 1.7, 0.3, 0.2), (3, 0.8)),
+    ((8, 6, 4, 10), 12, (1.3, 1.5, 0.5, 0.0158), (4, 0.4)),
+]
+
+
+class Lat:
+    def __init__(self, dims, L5, act, gseed):
+        self.dims, self.L5, self.act = dims, L5, act
+        self.U = synth.random_gauge(dims, gseed[0], gseed[1])
+        self.ctx = M.mdwf_create(dims, 0)
+        M.mdwf_load_gauge(self.ctx, 0, self.U, 1)
+        M.mdwf_set_action(self.ctx, 0, *act, L5)
+        self.shape = (L5,) + tuple(reversed(dims)) + (4, 3)
+
+    def close(self):
+        M.mdwf_destroy(self.ctx)
+
+
+@pytest.fixture(scope='module', params=range(len(CASES)))
+def lat(request):
+    L = Lat(*CASES[request.param])
+    yield L
+    L.close()
+
+
+@pytest.mark.parametrize('out_parity', [-1, 0, 1])
+@pytest.mark.parametrize('dagger', [0, 1])
+def test_dslash_fp64(lat, out_parity, dagger):
+    psi = synth.gaussian_spinor(lat.shape, 11)
+    out = M.mdwf_apply_dslash(lat.ctx, 0, psi, out_parity, dagger)
+    ref = O.hopping(lat.U, psi, True, bool(dagger))
+    if out_parity >= 0:
+        mask = O.parity_mask(lat.dims)
+        ref = O.restrict(ref, mask if out_parity == 0 else 1 - mask)
+    assert _rel(out, ref) < 1e-13
+
+
+@pytest.mark.parametrize('dagger', [0, 1])
+def test_mdwf_fp64(lat, dagger):
+    psi = synth.gaussian_spinor(lat.shape, 12)
+    out = M.mdwf_apply_mdwf(lat.ctx, 0, psi, dagger)
+    f = O.mobius_dag if dagger else O.mobius
+    assert _rel(out, f(lat.U, psi, *lat.act)) < 1e-13
+
+
+@pytest.mark.parametrize('op', ['A', 'B', 'Ainv'])
+@pytest.mark.parametrize('dagger', [0, 1])
+def test_fifth_dimension_ops(lat, op, dagger):
+    psi = synth.gaussian_spinor(lat.shape, 13)
+    out = M.mdwf_apply_5d(lat.ctx, 0, op, psi, dagger)
+    M5, b5, c5, mf = lat.act
+    ref = {'A': lambda v: O.op_A(v, M5, b5, c5, mf, bool(dagger)),
+           'B': lambda v: O.op_B(v, b5, c5, mf, bool(dagger)),
+           'Ainv': lambda v: O.op_A_inv(v, M5, b5, c5, mf, bool(dagger))}[op](psi)
+    assert _rel(out, ref) < 1e-13
+
+
+@pytest.mark.parametrize('precision,tol', [('double', 1e-13), ('single', 2e-6), ('half', 4e-3), ('bf16', 3e-2)])
+@pytest.mark.parametrize('dagger', [0, 1])
+def test_schur_operator(lat, precision, tol, dagger):
+    ev = O.parity_mask(lat.dims)
+    psi = O.restrict(synth.gaussian_spinor(lat.shape, 14), ev)
+    out = M.mdwf_apply_schur(lat.ctx, 0, psi, dagger, precision)
+    f = O.schur_op_dag if dagger else O.schur_op
+    assert _rel(out, f(lat.U, psi, *lat.act)) < tol
+
+
+def test_make_source(lat):
+    eta = synth.gaussian_spinor(tuple(reversed(lat.dims)) + (4, 3), 15)
+    out = M.mdwf_make_source(lat.ctx, 0, eta)
+    M5, b5, c5, mf = lat.act
+    assert _rel(out, O.make_source(lat.U, eta, M5, c5, lat.L5)) < 1e-13
+
+
+def test_time_boundary_periodic_option():
+    dims, L5 = (4, 2, 2, 4), 3
+    U = synth.random_gauge(dims, 5, 0.5)
+    ctx = M.mdwf_create(dims, 0)
+    try:
+        M.mdwf_load_gauge(ctx, 0, U, 0)
+        M.mdwf_set_action(ctx, 0, 1.3, 1.5, 0.5, 0.1, L5)
+        psi = synth.gaussian_spinor((L5, 4, 2, 2, 4, 4, 3), 16)
+        out = M.mdwf_apply_dslash(ctx, 0, psi, -1, 0)
+        assert _rel(out, O.hopping(U, psi, False)) < 1e-13
+    finally:
+        M.mdwf_destroy(ctx)
+
+
+# ---------------------------------------------------------------------------
+# solves
+# ---------------------------------------------------------------------------
+def _check_solution(lat, b, x, st, tol=1e-10, mf=None):
+    M5, b5, c5, mf0 = lat.act
+    mf = mf0 if mf is None else mf
+    res = O.true_residual(lat.U, b, x, M5, b5, c5, mf)
+    assert st['converged'] and st['rel_true_resid'] <= tol
+    assert res <= tol, res
+    assert abs(res - st['rel_true_resid']) <= 0.05 * tol + 1e-3 * res
+    return res
+
+
+@pytest.mark.parametrize('precision', ['double', 'single', 'half', 'bf16'])
+def test_solve_point_source_oracle_workload(precision):
+    """4^3 x 8, L5 = 4, M5 = 1.3, b5 = 1.5, c5 = 0.5, mf = 0.1, exp(0.3 i H) links,
+    point source (spin 0, colour 0, origin) as a 5D unit vector on the s = 0 slice."""
+    L = Lat(*CASES[0])
+    try:
+        b = np.zeros(L.shape, dtype=np.complex128)
+        b[0, 0, 0, 0, 0, 0, 0] = 1.0
+        x, st = M.mdwf_solve(L.ctx, 0, b, 1e-10, M.mdwf_default_opts(precision=precision))
+        _check_solution(L, b, x, st)
+        ref, _ = O.solve_schur(L.U, b, *L.act, tol=1e-13)
+        assert _rel(x, ref) < 1e-8
+    finally:
+        L.close()
+
+
+@pytest.mark.parametrize('precision', ['single', 'half', 'bf16'])
+def test_solve_batch_spin_colour_and_masses(precision):
+    """12 spin-colour wall sources with three masses in one batch (flowed links)."""
+    dims, L5 = (4, 4, 4, 8), 6
+    act = (1.2, 1.25, 0.25, 0.02)
+    U = synth.flowed_gauge(dims, 7, 0.4, flow_t=0.2, flow_eps=0.02)
+    ctx = M.mdwf_create(dims, 0)
+    try:
+        M.mdwf_load_gauge(ctx, 0, U, 1)
+        M.mdwf_set_action(ctx, 0, *act, L5)
+        srcs, masses = [], []
+        for k in range(12):
+            srcs.append(M.mdwf_make_source(ctx, 0, synth.point_source_4d(dims, k // 3, k % 3)))
+            masses.append((0.02, 0.05, 0.1)[k % 3])
+        xs, stats = M.mdwf_solve_batch(ctx, 0, srcs, 1e-10, masses=masses,
+                                       opts=M.mdwf_default_opts(precision=precision))
+        for b, x, st, m in zip(srcs, xs, stats, masses):
+            res = O.true_residual(U, b, x, act[0], act[1], act[2], m)
+            assert st['converged'] and res <= 1e-10, (st, res)
+        # one system against the oracle's own solution
+        ref, _ = O.solve_schur(U, srcs[4], act[0], act[1], act[2], masses[4], tol=1e-13)
+        assert _rel(xs[4], ref) < 1e-7
+    finally:
+        M.mdwf_destroy(ctx)
+
+
+def test_batch_result_same_alone_and_in_mix():
+    """A system solved alone and inside a batch of other systems gives the same x
+    (the reductions of one slot do not depend on the other slots)."""
+    dims, L5 = (4, 4, 4, 8), 4
+    act = (1.3, 1.5, 0.5, 0.1)
+    U = synth.random_gauge(dims, 9, 0.3)
+    ctx = M.mdwf_create(dims, 0)
+    try:
+        M.mdwf_load_gauge(ctx, 0, U, 1)
+        M.mdwf_set_action(ctx, 0, *act, L5)
+        shape = (L5, 8, 4, 4, 4, 4, 3)
+        target = synth.gaussian_spinor(shape, 100)
+        others = [synth.gaussian_spinor(shape, 101 + k) for k in range(5)]
+        opts = M.mdwf_default_opts(precision='half')
+        alone, st_a = M.mdwf_solve_batch(ctx, 0, [target], 1e-10, masses=[0.1], opts=opts)
+        mix, st_m = M.mdwf_solve_batch(ctx, 0, others[:3] + [target] + others[3:], 1e-10,
+                                       masses=[0.05, 0.2, 0.1, 0.1, 0.3, 0.1], opts=opts)
+        assert st_a[0]['iters'] == st_m[3]['iters']
+        assert np.array_equal(alone[0], mix[3])
+    finally:
+        M.mdwf_destroy(ctx)
+
+
+def test_solve_errors():
+    dims = (4, 4, 4, 4)
+    ctx = M.mdwf_create(dims, 0)
+    try:
+        with pytest.raises(M.MdwfError) as e:
+            M.mdwf_set_action(ctx, 0, 1.3, 1.5, 0.5, 0.1, 1)
+        assert e.value.code == M.MDWF_ERR_ARG
+        U = synth.random_gauge(dims, 1, 0.3)
+        U[0, 0, 0, 0, 0, 0, 0] = np.nan
+        with pytest.raises(M.MdwfError) as e:
+            M.mdwf_load_gauge(ctx, 0, U, 1)
+        assert e.value.code == M.MDWF_ERR_NONFINITE
+        M.mdwf_load_gauge(ctx, 0, synth.random_gauge(dims, 1, 0.3), 1)
+        M.mdwf_set_action(ctx, 0, 1.3, 1.5, 0.5, 0.1, 4)
+        b = synth.gaussian_spinor((4, 4, 4, 4, 4, 4, 3), 1)
+        with pytest.raises(M.MdwfError) as e:
+            M.mdwf_solve(ctx, 0, b, 1e-10, M.mdwf_default_opts(max_iter=3))
+        assert e.value.code == M.MDWF_ERR_NOT_CONVERGED
+        b[0, 0, 0, 0, 0, 0, 0] = np.inf
+        with pytest.raises(M.MdwfError) as e:
+            M.mdwf_solve(ctx, 0, b, 1e-10)
+        assert e.value.code == M.MDWF_ERR_NONFINITE
+        with pytest.raises(M.MdwfError) as e:
+            M.mdwf_apply_mdwf(ctx, 5, b, 0)
+        assert e.value.code == M.MDWF_ERR_STATE
+    finally:
+        M.mdwf_destroy(ctx)
