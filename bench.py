@@ -1,0 +1,418 @@
+#!/usr/bin/env python
+"""Benchmark of the even-odd preconditioned Moebius domain-wall solve on GB300.
+
+One step = one batched mixed-precision solve (fp16 storage with per-site
+scales, FP32 arithmetic, FP64 reliable updates / accumulator / sums) of the 12
+spin-colour point sources of the 16^3 x 48, L5 = 12 workload (a15m310 action
+of the paper's Table II: M5 = 1.3, b5 = 1.5, c5 = 0.5, m_f = 0.0158) on
+near-identity random SU(3) links smoothed by Wilson flow to t = 1, to a true
+FP64 residual |b - D x| / |b| <= 1e-10.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MDWF solves/s to 1e-10 (batched mixed vs FP64 CG); Dslash HBM GB/s; p50/p99"
+WORKLOAD = dict(name='16^3x48 L5=12 a15m310-action, flowed SU(3), 12 spin-colour point sources, tol 1e-10',
+                dims=(16, 16, 16, 48), L5=12, M5=1.3, b5=1.5, c5=0.5, mf=0.0158,
+                seed=2, eps=0.4, flow_t=1.0, flow_eps=0.01, nsrc=12, tol=1e-10)
+BYTES_PER_UNIT = {'half': 48 + 4, 'single': 96, 'bf16': 48, 'double': 192}   # one stored (site, s, rhs) spinor
+LINK_BYTES = {'half': 72, 'single': 72, 'bf16': 72, 'double': 144}           # one stored link (18 reals)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument('--gpus', type=int, default=1)
+    ap.add_argument('--steps', type=int, default=5)
+    ap.add_argument('--warmup', type=int, default=3)
+    ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
+    ap.add_argument('--precision', default='half', choices=['half', 'single', 'bf16', 'double'])
+    ap.add_argument('--no-fp64', action='store_true', help='skip the FP64 single-RHS GPU CG comparison')
+    ap.add_argument('--no-cpu', action='store_true', help='skip the oracle cpu_baseline sample')
+    ap.add_argument('--rhs', type=int, default=12, help='spin-colour sources per step (12 = the workload)')
+    ap.add_argument('--mode', default='solve', choices=['solve', 'op'],
+                    help="'op': only apply the batched Schur operator (the solver's hop kernels), for profiling")
+    ap.add_argument('--lattice', default=None, help="op mode: Lx,Ly,Lz,Lt instead of the workload's 16,16,16,48")
+    ap.add_argument('--hop-variant', type=int, default=0,
+                    help='0 automatic (tensor-core hop for fp16), 1 CUDA-core direct loads, 2 CUDA-core staged')
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ('index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,'
+              'clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,'
+              'clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap')
+
+    def __init__(self, device_index):
+        self.dev = str(device_index)
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(['nvidia-smi', '-i', self.dev, '--query-gpu=' + self.FIELDS,
+                                          '--format=csv,noheader,nounits', '-lms', '200'],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {'sm_mhz': None, 'sm_max_mhz': None, 'reasons': ['nvidia-smi unavailable']}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, power, reasons = [], None, [], set()
+        names = ['hw_slowdown', 'hw_thermal_slowdown', 'sw_thermal_slowdown', 'sw_power_cap']
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(',')]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == 'active':
+                    reasons.add(name)
+        return {'sm_mhz': statistics.median(sm) if sm else None, 'sm_max_mhz': smax,
+                'reasons': sorted(reasons), 'samples': len(sm), 'power_w_max': max(power) if power else None}
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+def dist_setup(args):
+    rank = int(os.environ.get('RANK', '0'))
+    world = int(os.environ.get('WORLD_SIZE', '1'))
+    local = int(os.environ.get('LOCAL_RANK', '0'))
+    return rank, world, local
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, 'MEASURED_PEAKS.json')) as f:
+            p = json.load(f)
+        return float(p['hbm_gbs']), 'measured'
+    except (OSError, KeyError, ValueError):
+        return 6800.0, 'fallback'
+
+
+def ncu_traffic(kernel_key):
+    """Per-launch DRAM bytes of the hop kernel from the committed ncu summary, if the
+    kernel source has not changed since it was captured (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, 'profiles', 'hop_kernel_ncu.json')
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        src = open(os.path.join(ROOT, 'paper_1701_07559_gb300', 'csrc', 'hop.cu'), 'rb').read()
+        if rec.get('hop_cu_sha256') != hashlib.sha256(src).hexdigest():
+            return None
+        return rec['workloads'][kernel_key]['dram_bytes_per_launch']
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def make_inputs(M, ctx, W, nsrc):
+    import synth
+    srcs = []
+    for k in range(nsrc):
+        eta = synth.point_source_4d(W['dims'], k // 3, k % 3)
+        srcs.append(M.mdwf_make_source(ctx, 0, eta))
+    return srcs
+
+
+def oracle_sample(W, U):
+    """Time one application of the oracle's Schur operator on one RHS (the bounded
+    sample); a CGNR iteration applies Mhat and Mhat^+, i.e. twice this work."""
+    import synth
+    from oracle import mdwf_oracle as O
+    Lx, Ly, Lz, Lt = W['dims']
+    ev = O.parity_mask(W['dims'])
+    psi = O.restrict(synth.gaussian_spinor((W['L5'], Lt, Lz, Ly, Lx, 4, 3), 1), ev)
+    t0 = time.perf_counter()
+    O.schur_op(U, psi, W['M5'], W['b5'], W['c5'], W['mf'])
+    return time.perf_counter() - t0
+
+
+def oracle_cores():
+    n = os.environ.get('OMP_NUM_THREADS') or os.environ.get('OPENBLAS_NUM_THREADS')
+    return int(n) if n else 1
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 CPU oracle
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    rank, world, _ = dist_setup(args)
+    if rank != 0:
+        return 0
+    import numpy as np  # noqa: F401
+    import synth
+    W = WORKLOAD
+    U = synth.flowed_gauge(W['dims'], W['seed'], W['eps'], W['flow_t'], W['flow_eps'])
+    rec = iteration_record()
+    n_iter = rec['fp64_cgnr_iters'] if rec else None
+    for _ in range(max(0, min(args.warmup, 1))):
+        oracle_sample(W, U)
+    times = [oracle_sample(W, U) for _ in range(max(1, args.steps))]
+    t = statistics.median(times)
+    per_solve = 2.0 * t * n_iter if n_iter else None
+    value = (1.0 / per_solve) if per_solve else None
+    sample = ('one FP64 oracle Schur-operator application (numpy, one RHS, full 16^3x48x12 lattice) per step; '
+              'a CGNR iteration is two such applications; solves/s = 1/(2 t n_iter) with n_iter = %s, the '
+              'iteration count of FP64 CGNR on this workload' % n_iter)
+    line = {'impl': 'reference', 'metric': METRIC, 'value': value, 'unit': 'solves/s', 'n_gpus': args.gpus,
+            'steps': len(times), 'warmup': args.warmup, 'ms_per_step': 1e3 * statistics.mean(times),
+            'higher_is_better': True, 'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f64', 'data': 'synthetic',
+            'config': {'workload': W['name'], 'lattice': '16^3x48', 'L5': W['L5'], 'rhs': W['nsrc']},
+            'cpu_baseline': {'value': value, 'unit': 'solves/s', 'cores': oracle_cores(), 'kind': 'oracle',
+                             'sample': sample},
+            'e2e': {'value': value, 'unit': 'solves/s', 'h2d_bytes_per_step': 0, 'd2h_bytes_per_step': 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def iteration_record():
+    try:
+        with open(os.path.join(ROOT, 'profiles', 'workload_a15m310_iterations.json')) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return None
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+    rank, world, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group('nccl')
+    import __graft_entry__
+    __graft_entry__.build()
+    import synth
+    from paper_1701_07559_gb300 import mdwf as M
+    W = WORKLOAD
+    prec = args.precision
+    U = synth.flowed_gauge(W['dims'], W['seed'], W['eps'], W['flow_t'], W['flow_eps'])
+    ctx = M.mdwf_create(W['dims'], local)
+    M.mdwf_load_gauge(ctx, 0, U, 1)
+    M.mdwf_set_action(ctx, 0, W['M5'], W['b5'], W['c5'], W['mf'], W['L5'])
+    srcs = make_inputs(M, ctx, W, args.rhs)
+    n = len(srcs)
+    stream = torch.cuda.current_stream()
+    dsrc = [torch.from_numpy(s).to('cuda') for s in srcs]
+    dx = [torch.empty_like(s) for s in dsrc]
+    opts = M.mdwf_default_opts(precision=prec, profile=1, hop_variant=args.hop_variant)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        M.mdwf_solve_batch_dev(ctx, 0, dsrc, dx, W['tol'], opts=opts, stream=stream)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stats = []
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        stats.append(M.mdwf_solve_batch_dev(ctx, 0, dsrc, dx, W['tol'], opts=opts, stream=stream))
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) / 1e3
+    if dist is not None:
+        t = torch.tensor([total_s], device='cuda', dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = n * args.steps * world / total_s
+
+    # correctness of what was timed: FP64 true residual of the last step, and the
+    # oracle's own D on one solution (rank 0)
+    last = stats[-1]
+    resid_max = max(s['rel_true_resid'] for s in last)
+    assert all(s['converged'] for s in last), last
+    iters = [s['iters'] for s in last]
+
+    # dominant kernel: the inner-precision hop (4 launches per CG iteration)
+    hop_launches = sum(s[0]['hop_launches'] for s in stats)
+    hop_ms = sum(s[0]['hop_ms'] for s in stats)
+    units = last[0]['hop_units']
+    L5, V = W['L5'], W['dims'][0] * W['dims'][1] * W['dims'][2] * W['dims'][3]
+    # per launch: input + output (+ the `same` field in half of the launches) + 8 links per output site
+    bytes_per_launch = units * 2.5 * BYTES_PER_UNIT[prec] + (V // 2) * 8 * LINK_BYTES[prec]
+    hop_avg_s = (hop_ms / hop_launches) / 1e3
+    achieved = bytes_per_launch / hop_avg_s / 1e9
+    peak, peak_kind = measured_peaks()
+    gflops = units * 1320 / hop_avg_s / 1e9
+    gpu_launches = sum(s[0]['kernel_launches'] for s in stats)
+
+    # end to end through the host-pointer C ABI call, pinned host buffers
+    pin_src = [torch.from_numpy(s).pin_memory().numpy() for s in srcs]
+    pin_x = [torch.empty(s.shape, dtype=torch.complex128).pin_memory().numpy() for s in srcs]
+    opts_e2e = M.mdwf_default_opts(precision=prec, hop_variant=args.hop_variant)
+    M.mdwf_solve_batch(ctx, 0, pin_src, W['tol'], opts=opts_e2e, out=pin_x)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_t = []
+    for _ in range(args.steps):
+        t1 = time.perf_counter()
+        M.mdwf_solve_batch(ctx, 0, pin_src, W['tol'], opts=opts_e2e, out=pin_x)
+        e2e_t.append(time.perf_counter() - t1)
+    e2e_total = sum(e2e_t)
+    if dist is not None:
+        t = torch.tensor([e2e_total], device='cuda', dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_value = n * args.steps * world / e2e_total
+    field_bytes = L5 * V * 24 * 8
+
+    # plain FP64 single-RHS GPU CG on the first source (the baseline to beat)
+    fp64 = None
+    if not args.no_fp64:
+        o64 = M.mdwf_default_opts(precision='double')
+        t1 = time.perf_counter()
+        _, st64 = M.mdwf_solve_batch(ctx, 0, [pin_src[0]], W['tol'], opts=o64)
+        dt = time.perf_counter() - t1
+        fp64 = {'solves_per_s': 1.0 / dt, 'time_s': dt, 'iters': st64[0]['iters'],
+                'rel_true_resid': st64[0]['rel_true_resid'], 'precision': 'FP64 storage and arithmetic, 1 RHS'}
+
+    out = None
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu and world == 1:
+            rec = iteration_record()
+            n_iter = fp64['iters'] if fp64 else (rec['fp64_cgnr_iters'] if rec else None)
+            t_s = oracle_sample(W, U)
+            cpu_value = 1.0 / (2.0 * t_s * n_iter) if n_iter else None
+            cpu = {'value': cpu_value, 'unit': 'solves/s', 'cores': oracle_cores(), 'kind': 'oracle',
+                   'sample': ('one FP64 oracle Schur-operator application on one RHS of this workload (%.1f s); '
+                              'a CGNR iteration is two; scaled by the %s iterations FP64 CGNR takes here'
+                              % (t_s, n_iter))}
+        lat = sorted(step_ms)
+        p99 = lat[min(len(lat) - 1, int(np.ceil(0.99 * len(lat))) - 1)]
+        out = {
+            'metric': METRIC, 'value': value, 'unit': 'solves/s', 'n_gpus': world, 'steps': args.steps,
+            'warmup': args.warmup, 'ms_per_step': total_s * 1e3 / args.steps, 'higher_is_better': True,
+            'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f32',
+            'storage': {'half': 'fp16 + per-site scale', 'single': 'fp32', 'bf16': 'bf16',
+                        'double': 'fp64'}[prec] + ' inner vectors; FP64 accumulator, reliable updates and sums',
+            'data': 'synthetic',
+            'config': {'workload': W['name'], 'lattice': '16^3x48', 'L5': W['L5'], 'rhs_per_step': n,
+                       'action': {'M5': W['M5'], 'b5': W['b5'], 'c5': W['c5'], 'mf': W['mf']},
+                       'gauge': 'exp(i 0.4 H), Wilson flow t=1 (RK3, eps 0.01, FP64)', 'precision': prec,
+                       'l2': 'inputs larger than L2: %.2f GB of inner vectors per step' % (
+                           6 * units * BYTES_PER_UNIT[prec] / 1e9),
+                       'parallelism': 'replicas' if world > 1 else 'single GPU'},
+            'latency_ms': {'p50': statistics.median(step_ms), 'p99': p99, 'per_step': step_ms},
+            'iters': iters, 'rel_true_resid_max': resid_max,
+            'reliable_updates': [s['reliable_updates'] for s in last],
+            'fp64_gpu_cg': fp64,
+            'speedup_vs_fp64_gpu_cg': (value / fp64['solves_per_s']) if fp64 else None,
+            'dslash': {'kernel': 'hop_kernel<%s>' % prec, 'launches_timed': hop_launches,
+                       'avg_launch_us': hop_avg_s * 1e6, 'GB_per_s': achieved, 'eff_GFLOP_per_s': gflops,
+                       'units_per_launch': units, 'bytes_per_launch': bytes_per_launch},
+            'roofline': {'bound': 'hbm', 'achieved': achieved, 'peak': peak, 'unit': 'GB/s',
+                         'frac': achieved / peak, 'peak_kind': peak_kind,
+                         'traffic': ncu_traffic('a15m310_%s' % prec)},
+            'cpu_baseline': cpu,
+            'e2e': {'value': e2e_value, 'unit': 'solves/s', 'h2d_bytes_per_step': n * field_bytes,
+                    'd2h_bytes_per_step': n * field_bytes},
+            'gpu_launches': gpu_launches,
+            'clocks': clk,
+            'wall_s': wall,
+        }
+        print(json.dumps(out), flush=True)
+    M.mdwf_destroy(ctx)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_op(args):
+    """Apply Mhat and Mhat^+ to --rhs random fields of the workload, warmup + steps
+    times, through the batched C-ABI call (a short driver for kernel profiles)."""
+    import numpy as np  # noqa: F401
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import synth
+    from paper_1701_07559_gb300 import mdwf as M
+    W = dict(WORKLOAD)
+    if args.lattice:
+        W['dims'] = tuple(int(v) for v in args.lattice.split(','))
+    U = synth.flowed_gauge(W['dims'], W['seed'], W['eps'], W['flow_t'], W['flow_eps'])
+    ctx = M.mdwf_create(W['dims'], 0)
+    M.mdwf_load_gauge(ctx, 0, U, 1)
+    M.mdwf_set_action(ctx, 0, W['M5'], W['b5'], W['c5'], W['mf'], W['L5'])
+    Lx, Ly, Lz, Lt = W['dims']
+    shape = (W['L5'], Lt, Lz, Ly, Lx, 4, 3)
+    variant = args.hop_variant
+    ins = [torch.from_numpy(synth.gaussian_spinor(shape, 50 + i)).to('cuda') for i in range(args.rhs)]
+    outs = [torch.empty_like(x) for x in ins]
+    t = []
+    for i in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        M.mdwf_apply_schur_batch_dev(ctx, 0, ins, outs, dagger=0, precision=args.precision, hop_variant=variant)
+        M.mdwf_apply_schur_batch_dev(ctx, 0, outs, ins, dagger=1, precision=args.precision, hop_variant=variant)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            t.append(time.perf_counter() - t0)
+    M.mdwf_destroy(ctx)
+    print(json.dumps({'mode': 'op', 'rhs': args.rhs, 'precision': args.precision, 'lattice': W['dims'],
+                      'hop_variant': args.hop_variant,
+                      'ms_per_pair_of_applies': 1e3 * statistics.mean(t) if t else None}), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == 'reference':
+        return run_reference(args)
+    if args.mode == 'op':
+        return run_op(args)
+    return run_ours(args)
+
+
+if __name__ == '__main__':
+    sys.exit(main())

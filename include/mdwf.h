@@ -65,17 +65,28 @@ typedef struct {
   double delta;    /* reliable update when |r| < delta * max |r| since the last one (default 0.1) */
   int chunk;       /* CG iterations per device launch sequence between host checks (default 16) */
   int use_graph;   /* capture each chunk in a CUDA graph (default 1) */
-  int nsb;         /* half-lattice sites per thread block tile (default 2; 0 = default) */
-  int reserved[6];
+  int nsb;         /* half-lattice sites per thread block (0 = chosen by the library) */
+  int profile;     /* 1: time every inner-precision hop launch with CUDA events (stats.hop_*) */
+  double wait_timeout_s; /* bound of every device-side wait (default 2 s); a wait that runs out ends
+                            the call with MDWF_ERR_TIMEOUT and leaves the context usable */
+  int timeout_test;      /* testing only: 1 makes each staged-copy wait expect bytes that never
+                            arrive, so the bound above must end the call with MDWF_ERR_TIMEOUT */
+  int hop_variant;       /* 0: automatic (tensor-core hop for fp16 storage when a block holds whole
+                            sites, else CUDA-core); 1: CUDA-core hop with direct neighbour loads;
+                            2: CUDA-core hop with neighbours staged in shared memory by bulk copies */
+  int reserved[2];
 } mdwf_solver_opts;
 
 typedef struct {
   int iters;             /* CG iterations */
-  int reliable_updates;  /* FP64 residual recomputations (including the final check) */
+  int reliable_updates;  /* FP64 residual recomputations (including the initial one) */
   int converged;         /* 1 if rel_true_resid <= tol */
-  int reserved0;
+  int hop_launches;      /* inner-precision hop launches timed (opts.profile), batch total */
   double rel_true_resid; /* ||b - D x|| / ||b|| of the returned x, in FP64 on the full lattice */
   double time_s;         /* wall time of the call */
+  double hop_ms;         /* summed device time of those launches (opts.profile), batch total */
+  long long kernel_launches; /* kernels this call put on the GPU, batch total */
+  long long hop_units;   /* (site, slice, RHS) units per inner hop launch */
 } mdwf_solve_stats;
 
 /* Fill opts with the defaults listed above. */
@@ -153,6 +164,17 @@ int mdwf_solve_batch(mdwf_ctx* ctx, int cfg_id, int n, const double* const* srcs
 int mdwf_solve_batch_dev(mdwf_ctx* ctx, int cfg_id, int n, const double* const* srcs, const double* masses,
                          double* const* xs, double tol, const mdwf_solver_opts* opts, mdwf_solve_stats* stats,
                          void* stream);
+
+/* The Schur operator of the solver for n right-hand sides at once, on device
+ * fields (layout above): out_i = Mhat(m_i) in_i (dagger = 0) or Mhat(m_i)^+ in_i,
+ * with m_i = masses[i] (host array; NULL = the action's m_f).  It runs the same
+ * kernels, tiling and storage precision (MDWF_PREC_*) as the CG iterations of
+ * mdwf_solve_batch; odd sites of in_i are ignored and odd sites of out_i set
+ * to zero.  hop_variant as in mdwf_solver_opts.  Returns after the work on
+ * `stream` has finished.
+ * Errors: ARG, STATE, NOMEM, CUDA, TIMEOUT. */
+int mdwf_apply_schur_batch_dev(mdwf_ctx* ctx, int cfg_id, int n, const double* const* in, double* const* out,
+                               const double* masses, int dagger, int precision, int hop_variant, void* stream);
 
 /* Device-pointer variants of the operator applies, on `stream` (asynchronous). */
 int mdwf_apply_dslash_dev(mdwf_ctx* ctx, int cfg_id, const double* in, double* out, int out_parity, int dagger,

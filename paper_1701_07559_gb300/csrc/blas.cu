@@ -29,16 +29,17 @@ __device__ __forceinline__ Unit unit_of(const Tiling& tl, long Vh, int L5, int N
   return x;
 }
 
-// Per-slot sum of `v` over the block's (site, s) units, written to partials[tile][r].
-__device__ __forceinline__ void block_partial(double v, const Unit& x, const Tiling& tl, int L5, int N,
+// Per-site, per-slot sum of `v` over the L5 slices (fixed order), written to
+// partials[r][h]; the final sum over sites is then independent of the tiling.
+__device__ __forceinline__ void block_partial(double v, const Unit& x, const Tiling& tl, int L5, long Vh,
                                               double* __restrict__ partials) {
   __shared__ double sred[1024];
   sred[threadIdx.x] = v;
   __syncthreads();
-  if (x.s == 0 && x.site_l == 0 && x.r < N) {
+  if (x.s == 0 && x.valid) {
     double sum = 0.0;
-    for (int k = 0; k < tl.nsb * L5; k++) sum += sred[k * tl.rt + x.r_l];
-    partials[(long)blockIdx.x * N + x.r] = sum;
+    for (int k = 0; k < L5; k++) sum += sred[(x.site_l * L5 + k) * tl.rt + x.r_l];
+    partials[(long)x.r * Vh + x.h] = sum;
   }
 }
 
@@ -111,16 +112,18 @@ __global__ void k_axpy_x_rho(SX* __restrict__ xv, const S* __restrict__ p, const
     load24<S, T>(q, q_nrm, x.u, qv);
     load24<S, T>(rho, rho_nrm, x.u, rv);
     load24<SX, TX>(xv, nullptr, x.u, xv_);
+    T n2t = 0;
 #pragma unroll
     for (int i = 0; i < 24; i++) {
       xv_[i] += (TX)(a * pv[i]);
       rv[i] -= a * qv[i];
-      n2 += (double)rv[i] * (double)rv[i];
+      n2t += rv[i] * rv[i];
     }
+    n2 = (double)n2t;
     store24<SX, TX>(xv, nullptr, x.u, xv_);
     store24<S, T>(rho, rho_nrm, x.u, rv);
   }
-  block_partial(n2, x, tl, L5, N, partials);
+  block_partial(n2, x, tl, L5, Vh, partials);
 }
 
 // p = r + beta_r p
@@ -166,18 +169,21 @@ __global__ void k_norm2(const S* __restrict__ v, const float* __restrict__ v_nrm
   if (x.valid && (!mask || mask[x.r])) {
     T a[24];
     load24<S, T>(v, v_nrm, x.u, a);
+    T n2t = 0;
 #pragma unroll
-    for (int i = 0; i < 24; i++) n2 += (double)a[i] * (double)a[i];
+    for (int i = 0; i < 24; i++) n2t += a[i] * a[i];
+    n2 = (double)n2t;
   }
-  block_partial(n2, x, tl, L5, N, partials);
+  block_partial(n2, x, tl, L5, Vh, partials);
 }
 
-// out[r] = sum_tiles partials[tile][r], fixed order: thread t takes tiles t, t+T, ..., then a fixed tree.
-__global__ void k_finalize(const double* __restrict__ partials, long ntiles, int N, double* __restrict__ out) {
+// out[r] = sum_h partials[r][h], fixed order: thread t takes sites t, t+T, ..., then a fixed tree.
+__global__ void k_finalize(const double* __restrict__ partials, long nsites, int N, double* __restrict__ out) {
   __shared__ double sh[256];
   const int r = blockIdx.x;
   double s = 0.0;
-  for (long k = threadIdx.x; k < ntiles; k += blockDim.x) s += partials[k * N + r];
+  const double* p = partials + (long)r * nsites;
+  for (long k = threadIdx.x; k < nsites; k += blockDim.x) s += p[k];
   sh[threadIdx.x] = s;
   __syncthreads();
   for (int w = blockDim.x / 2; w > 0; w >>= 1) {
@@ -185,6 +191,96 @@ __global__ void k_finalize(const double* __restrict__ partials, long ntiles, int
     __syncthreads();
   }
   if (threadIdx.x == 0) out[r] = sh[0];
+}
+
+// u = B x on one parity: P_+ half b5 x_s + c5 x_{s-1}, P_- half b5 x_s + c5 x_{s+1},
+// with x_{-1} = -m x_{L5-1} and x_{L5} = -m x_0.
+template <typename S>
+__global__ void k_bop(const S* __restrict__ xv, const float* __restrict__ x_nrm, S* __restrict__ uv,
+                      float* __restrict__ u_nrm, Fifth<typename StoreTraits<S>::T> f, Tiling tl, long Vh, int L5, int N,
+                      const int* __restrict__ mask) {
+  using T = typename StoreTraits<S>::T;
+  Unit x = unit_of(tl, Vh, L5, N);
+  if (!x.valid || (mask && !mask[x.r])) return;
+  const T m = f.mass[x.r];
+  const int s_dn = x.s == 0 ? L5 - 1 : x.s - 1, s_up = x.s == L5 - 1 ? 0 : x.s + 1;
+  const T w_dn = x.s == 0 ? -m : T(1), w_up = x.s == L5 - 1 ? -m : T(1);
+  T y[24], up[12], lo[12];
+  load24<S, T>(xv, x_nrm, x.u, y);
+  load_part<S, T>(xv, x_nrm, (x.h * L5 + s_dn) * N + x.r, 0, up);
+  load_part<S, T>(xv, x_nrm, (x.h * L5 + s_up) * N + x.r, 1, lo);
+#pragma unroll
+  for (int i = 0; i < 12; i++) y[i] = f.b5 * y[i] + f.c5 * w_dn * up[i];
+#pragma unroll
+  for (int i = 0; i < 12; i++) y[12 + i] = f.b5 * y[12 + i] + f.c5 * w_up * lo[i];
+  store24<S, T>(uv, u_nrm, x.u, y);
+}
+
+// p = r + beta_r p, then u = B p (the new p of the neighbouring slices comes from
+// shared memory: a block holds every slice of its sites).
+template <typename S>
+__global__ void k_xpay_b(const S* __restrict__ r, const float* __restrict__ r_nrm, S* __restrict__ p,
+                         float* __restrict__ p_nrm, S* __restrict__ uv, float* __restrict__ u_nrm,
+                         const double* __restrict__ beta, Fifth<typename StoreTraits<S>::T> f, Tiling tl, long Vh,
+                         int L5, int N, const int* __restrict__ active) {
+  using T = typename StoreTraits<S>::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sP = reinterpret_cast<T*>(smem_raw);
+  Unit x = unit_of(tl, Vh, L5, N);
+  const bool act = x.valid && (!active || active[x.r]);
+  T pv[24];
+#pragma unroll
+  for (int i = 0; i < 24; i++) pv[i] = 0;
+  if (act) {
+    const T b = (T)beta[x.r];
+    T rv[24];
+    load24<S, T>(r, r_nrm, x.u, rv);
+    load24<S, T>(p, p_nrm, x.u, pv);
+#pragma unroll
+    for (int i = 0; i < 24; i++) pv[i] = rv[i] + b * pv[i];
+    store24<S, T>(p, p_nrm, x.u, pv);
+  }
+#pragma unroll
+  for (int i = 0; i < 24; i++) sP[threadIdx.x * 25 + i] = pv[i];
+  __syncthreads();
+  if (!act) return;
+  const T m = f.mass[x.r];
+  const int s_dn = x.s == 0 ? L5 - 1 : x.s - 1, s_up = x.s == L5 - 1 ? 0 : x.s + 1;
+  const T w_dn = x.s == 0 ? -m : T(1), w_up = x.s == L5 - 1 ? -m : T(1);
+  const T* nd = sP + (size_t)((x.site_l * L5 + s_dn) * tl.rt + x.r_l) * 25;
+  const T* nu = sP + (size_t)((x.site_l * L5 + s_up) * tl.rt + x.r_l) * 25;
+  T y[24];
+#pragma unroll
+  for (int i = 0; i < 12; i++) y[i] = f.b5 * pv[i] + f.c5 * w_dn * nd[i];
+#pragma unroll
+  for (int i = 12; i < 24; i++) y[i] = f.b5 * pv[i] + f.c5 * w_up * nu[i];
+  store24<S, T>(uv, u_nrm, x.u, y);
+}
+
+// rho = S(bhat - q) with bhat in FP64 and q in FP32 (the residual of a reliable
+// update computed with FP32 arithmetic); partial |bhat - q|^2 in FP64.
+template <typename S>
+__global__ void k_resid_update(const double* __restrict__ bhat, const float* __restrict__ q, S* __restrict__ rho,
+                               float* __restrict__ rho_nrm, Tiling tl, long Vh, int L5, int N,
+                               const int* __restrict__ mask, double* __restrict__ partials) {
+  using T = typename StoreTraits<S>::T;
+  Unit x = unit_of(tl, Vh, L5, N);
+  double n2 = 0.0;
+  if (x.valid && (!mask || mask[x.r])) {
+    double b[24];
+    float qv[24];
+    load24<double, double>(bhat, nullptr, x.u, b);
+    load24<float, float>(q, nullptr, x.u, qv);
+    T o[24];
+#pragma unroll
+    for (int i = 0; i < 24; i++) {
+      double v = b[i] - (double)qv[i];
+      n2 += v * v;
+      o[i] = (T)v;
+    }
+    store24<S, T>(rho, rho_nrm, x.u, o);
+  }
+  block_partial(n2, x, tl, L5, Vh, partials);
 }
 
 // ---------------------------------------------------------------------------
@@ -245,6 +341,34 @@ cudaError_t norm2_partials(const S* v, const float* v_nrm, const Tiling& t, long
   return cudaGetLastError();
 }
 
+template <typename S>
+cudaError_t bop(const S* x, const float* x_nrm, S* u, float* u_nrm, const Fifth<typename StoreTraits<S>::T>& f,
+                const Tiling& t, long Vh, int L5, int N, const int* mask, cudaStream_t st) {
+  k_bop<S><<<tile_grid(t), t.threads, 0, st>>>(x, x_nrm, u, u_nrm, f, t, Vh, L5, N, mask);
+  return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t xpay_b(const S* r, const float* r_nrm, S* p, float* p_nrm, S* u, float* u_nrm, const double* beta,
+                   const Fifth<typename StoreTraits<S>::T>& f, const Tiling& t, long Vh, int L5, int N,
+                   const int* active, cudaStream_t st) {
+  using T = typename StoreTraits<S>::T;
+  size_t smem = (size_t)t.threads * 25 * sizeof(T);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_xpay_b<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_xpay_b<S><<<tile_grid(t), t.threads, smem, st>>>(r, r_nrm, p, p_nrm, u, u_nrm, beta, f, t, Vh, L5, N, active);
+  return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t resid_update(const double* bhat, const float* q, S* rho, float* rho_nrm, const Tiling& t, long Vh, int L5,
+                         int N, const int* mask, double* partials, cudaStream_t st) {
+  k_resid_update<S><<<tile_grid(t), t.threads, 0, st>>>(bhat, q, rho, rho_nrm, t, Vh, L5, N, mask, partials);
+  return cudaGetLastError();
+}
+
 cudaError_t finalize(const double* partials, long ntiles, int N, double* out, cudaStream_t st) {
   k_finalize<<<N, 256, 0, st>>>(partials, ntiles, N, out);
   return cudaGetLastError();
@@ -258,6 +382,19 @@ cudaError_t finalize(const double* partials, long ntiles, int N, double* out, cu
                                const int*, cudaStream_t);                                                       \
   template cudaError_t norm2_partials<S>(const S*, const float*, const Tiling&, long, int, int, const int*,      \
                                          double*, cudaStream_t);
+
+#define MDWF_INST_B(S)                                                                                           \
+  template cudaError_t bop<S>(const S*, const float*, S*, float*, const Fifth<StoreTraits<S>::T>&, const Tiling&,  \
+                              long, int, int, const int*, cudaStream_t);                                          \
+  template cudaError_t xpay_b<S>(const S*, const float*, S*, float*, S*, float*, const double*,                    \
+                                 const Fifth<StoreTraits<S>::T>&, const Tiling&, long, int, int, const int*,        \
+                                 cudaStream_t);                                                                    \
+  template cudaError_t resid_update<S>(const double*, const float*, S*, float*, const Tiling&, long, int, int,      \
+                                       const int*, double*, cudaStream_t);
+MDWF_INST_B(double)
+MDWF_INST_B(float)
+MDWF_INST_B(__half)
+MDWF_INST_B(__nv_bfloat16)
 
 MDWF_INST_S(double)
 MDWF_INST_S(float)

@@ -33,6 +33,19 @@ template <typename S>
 cudaError_t norm2_partials(const S* v, const float* v_nrm, const Tiling& t, long Vh, int L5, int N, const int* mask,
                            double* partials, cudaStream_t st);
 
+template <typename S>
+cudaError_t bop(const S* x, const float* x_nrm, S* u, float* u_nrm, const Fifth<typename StoreTraits<S>::T>& f,
+                const Tiling& t, long Vh, int L5, int N, const int* mask, cudaStream_t st);
+
+template <typename S>
+cudaError_t xpay_b(const S* r, const float* r_nrm, S* p, float* p_nrm, S* u, float* u_nrm, const double* beta,
+                   const Fifth<typename StoreTraits<S>::T>& f, const Tiling& t, long Vh, int L5, int N,
+                   const int* active, cudaStream_t st);
+
+template <typename S>
+cudaError_t resid_update(const double* bhat, const float* q, S* rho, float* rho_nrm, const Tiling& t, long Vh, int L5,
+                         int N, const int* mask, double* partials, cudaStream_t st);
+
 cudaError_t finalize(const double* partials, long ntiles, int N, double* out, cudaStream_t st);
 
 }  // namespace mdwf

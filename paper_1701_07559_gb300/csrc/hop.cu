@@ -233,10 +233,10 @@ __global__ void hop_kernel(HopArgs<S, T> a, Tiling tl) {
     double* sred = reinterpret_cast<double*>(smem_raw);
     sred[tid] = n2;
     __syncthreads();
-    if (s == 0 && site_l == 0 && r < a.N) {
+    if (s == 0 && valid) {
       double sum = 0.0;
-      for (int k = 0; k < tl.nsb * L5; k++) sum += sred[k * tl.rt + r_l];
-      a.partials[(long)blockIdx.x * a.N + r] = sum;
+      for (int k = 0; k < L5; k++) sum += sred[(site_l * L5 + k) * tl.rt + r_l];
+      a.partials[(long)r * a.g.Vh + h] = sum;
     }
   }
 }

@@ -39,6 +39,7 @@ struct Cfg {
   int anti = 1;
   double* U64 = nullptr;
   float* U32 = nullptr;
+  __half2* U16 = nullptr;   // fp16 links [parity][h][mu][3][3] for the tensor-core hop
   Action act;
 };
 
@@ -48,6 +49,7 @@ struct mdwf_ctx {
   std::map<int, Cfg> cfgs;
   std::string err;
   cudaStream_t stream = nullptr;
+  std::map<std::string, std::pair<void*, size_t>> ws;  // reusable device workspace
 };
 
 namespace {
@@ -213,6 +215,45 @@ struct FieldBuf {    // owning
   F<S> f() const { F<S> r; r.v = v.as<S>(); r.n = n.as<float>(); return r; }
 };
 
+// Event timing of hop launches: pairs of events around every launch, either
+// recorded directly (collected after the next stream synchronisation) or
+// captured into a CUDA graph (collected after each graph launch).
+struct Prof {
+  std::vector<cudaEvent_t> pool, gpool;
+  size_t used = 0, gused = 0;
+  bool capturing = false;
+  double ms = 0.0;
+  long long n = 0;
+  ~Prof() {
+    for (auto e : pool) cudaEventDestroy(e);
+    for (auto e : gpool) cudaEventDestroy(e);
+  }
+  cudaError_t record(cudaStream_t st) {
+    std::vector<cudaEvent_t>& v = capturing ? gpool : pool;
+    size_t& u = capturing ? gused : used;
+    if (u >= v.size()) {
+      cudaEvent_t e;
+      cudaError_t err = cudaEventCreate(&e);
+      if (err != cudaSuccess) return err;
+      v.push_back(e);
+    }
+    // inside a capture only an "external" record becomes an event node of the graph
+    return capturing ? cudaEventRecordWithFlags(v[u++], st, cudaEventRecordExternal) : cudaEventRecord(v[u++], st);
+  }
+  cudaError_t sum(const std::vector<cudaEvent_t>& v, size_t u) {
+    for (size_t i = 0; i + 1 < u; i += 2) {
+      float t = 0.f;
+      cudaError_t err = cudaEventElapsedTime(&t, v[i], v[i + 1]);
+      if (err != cudaSuccess) return err;
+      ms += t;
+      n += 1;
+    }
+    return cudaSuccess;
+  }
+  cudaError_t collect() { cudaError_t e = sum(pool, used); used = 0; return e; }   // after a sync
+  cudaError_t collect_graph() { return sum(gpool, gused); }                        // after a graph launch + sync
+};
+
 template <typename S, typename T>
 struct Op {
   Geom g;
@@ -220,6 +261,8 @@ struct Op {
   const T* U = nullptr;
   Tiling tl;
   cudaStream_t st = nullptr;
+  Prof* prof = nullptr;          // time hop launches when set
+  long long* launches = nullptr; // count launches when set
 
   // out = add + G same + kappa C H(in)   (hop) ; out = add + G in (local)
   cudaError_t run(bool hop, int out_par, int dagger, F<S> in, F<S> same, const T* G, F<S> add, const T* C, T kappa,
@@ -229,6 +272,14 @@ struct Op {
     a.in = in.v; a.in_nrm = in.n; a.same = same.v; a.same_nrm = same.n; a.add = add.v; a.add_nrm = add.n;
     a.out = out.v; a.out_nrm = out.n; a.U = U; a.Gm = G; a.Cm = C; a.kappa = kappa; a.active = active;
     a.partials = partials;
+    if (launches) *launches += 1;
+    if (prof && hop) {
+      cudaError_t e = prof->record(st);
+      if (e != cudaSuccess) return e;
+      e = launch_hop<S, T>(a, tl, hop, st);
+      if (e != cudaSuccess) return e;
+      return prof->record(st);
+    }
     return launch_hop<S, T>(a, tl, hop, st);
   }
   // q = Mhat p (dagger 0) or Mhat^+ p (dagger 1) on even sites; u, t scratch (even, odd).
@@ -264,11 +315,12 @@ Tiling tiling_for(const Geom& g, int L5, int N, int nsb, bool two_buffers) {
 // Scalar kernels of the batched CG (one thread per RHS slot)
 // ---------------------------------------------------------------------------
 struct Scal {
-  double *gamma, *gamma_prev, *alpha, *beta, *rho2, *rho2_max, *stop2, *qq, *rr, *tmp;
+  double *gamma, *gamma_prev, *alpha, *beta, *rho2, *rho2_max, *stop2, *qq, *rr, *tmp, *bhat2;
   int *active, *flags, *iters;
-  double delta2;
+  double delta2;  // periodic reliable update when |rho|^2 < delta2 * max |rho|^2 since the last one
+  double tau2;    // FP64 re-reference when |rho|^2 <= tau2 * |bhat|^2 (bhat = current reference residual)
 };
-enum { FLAG_INNER_DONE = 1, FLAG_UPDATE = 2, FLAG_DONE = 4 };
+enum { FLAG_INNER_DONE = 1, FLAG_UPDATE = 2, FLAG_DONE = 4, FLAG_REREF = 8 };
 
 __global__ void k_alpha(Scal c, int N) {
   int r = threadIdx.x;
@@ -281,7 +333,7 @@ __global__ void k_after_rho(Scal c, int N) {
     c.rho2[r] = v;
     if (v > c.rho2_max[r]) c.rho2_max[r] = v;
     if (v <= c.stop2[r]) { c.active[r] = 0; c.flags[r] |= FLAG_INNER_DONE; }
-    else if (v < c.delta2 * c.rho2_max[r]) c.flags[r] |= FLAG_UPDATE;
+    else if (v < c.delta2 * c.rho2_max[r] || v <= c.tau2 * c.bhat2[r]) c.flags[r] |= FLAG_UPDATE;
   }
 }
 __global__ void k_beta(Scal c, int N) {
@@ -294,21 +346,189 @@ __global__ void k_beta(Scal c, int N) {
     c.iters[r] += 1;
   }
 }
-__global__ void k_after_update(Scal c, int N, const int* umask) {
+// After a residual recomputed with FP32 arithmetic: its error is ~1e-7 |bhat|,
+// so it may declare convergence only once bhat itself is small (a re-reference
+// has happened); otherwise an FP64 re-reference is requested.
+__global__ void k_after_update(Scal c, int N, const int* um) {
   int r = threadIdx.x;
-  if (r < N && umask[r]) {
+  if (r < N && um[r]) {
     double v = c.tmp[r];
     c.rho2[r] = v;
     c.rho2_max[r] = v;
     c.gamma[r] = c.rr[r];
     c.beta[r] = c.gamma_prev[r] > 0.0 ? c.gamma[r] / c.gamma_prev[r] : 0.0;
-    if (c.flags[r] & FLAG_INNER_DONE) {
-      if (v <= c.stop2[r]) { c.flags[r] = FLAG_DONE; c.active[r] = 0; }
-      else { c.flags[r] = 0; c.active[r] = 1; }
-    } else {
-      c.flags[r] &= ~FLAG_UPDATE;
+    bool fine = c.bhat2[r] <= 1e11 * c.stop2[r];
+    if (v <= c.stop2[r] && fine) { c.flags[r] = FLAG_DONE; c.active[r] = 0; }
+    else if (v <= c.stop2[r] || v <= c.tau2 * c.bhat2[r]) { c.flags[r] = FLAG_REREF; c.active[r] = 1; }
+    else { c.flags[r] = 0; c.active[r] = 1; }
+  }
+}
+// After an FP64 re-reference (bhat <- rho, x_acc += x_hi).
+__global__ void k_after_reref(Scal c, int N, const int* um) {
+  int r = threadIdx.x;
+  if (r < N && um[r]) {
+    double v = c.tmp[r];
+    c.rho2[r] = v;
+    c.rho2_max[r] = v;
+    c.bhat2[r] = v;
+    c.gamma[r] = c.rr[r];
+    c.beta[r] = c.gamma_prev[r] > 0.0 ? c.gamma[r] / c.gamma_prev[r] : 0.0;
+    if (v <= c.stop2[r]) { c.flags[r] = FLAG_DONE; c.active[r] = 0; }
+    else { c.flags[r] = 0; c.active[r] = 1; }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Fast operator passes
+// ---------------------------------------------------------------------------
+template <typename S, typename T>
+struct FastOp {
+  Geom g;
+  int L5 = 0, N = 0, anti = 1;
+  const T* U = nullptr;
+  Tiling tl;
+  cudaStream_t st = nullptr;
+  Fifth<T> f;
+  Prof* prof = nullptr;
+  long long* launches = nullptr;
+  const StageInfo* stage = nullptr;   // neighbour staging through shared memory, when the tiling allows
+  const __half2* U16 = nullptr;       // fp16 links for the tensor-core hop
+  bool mma = false;                   // use the tensor-core hop (fp16 storage only)
+
+  cudaError_t dispatch(const FastArgs<S, T>& a, int epi) const {
+    if constexpr (std::is_same<S, __half>::value) {
+      if (mma) return launch_fast_mma(a, tl, epi, st);
+    }
+    return launch_fast<S, T>(a, tl, epi, st, stage);
+  }
+
+  cudaError_t run(int epi, int out_par, int dagger, F<S> in, F<S> same, F<S> add, T g_same, T kappa, F<S> out,
+                  const int* active, double* partials) const {
+    FastArgs<S, T> a;
+    a.g = g; a.L5 = L5; a.N = N; a.out_par = out_par; a.dagger = dagger; a.antiperiodic = anti;
+    a.in = in.v; a.in_nrm = in.n; a.same = same.v; a.same_nrm = same.n; a.add = add.v; a.add_nrm = add.n;
+    a.out = out.v; a.out_nrm = out.n; a.U = U; a.U16 = U16; a.f = f; a.g_same = g_same; a.kappa = kappa;
+    a.active = active;
+    a.partials = partials;
+    if (launches) *launches += 1;
+    if (prof) {
+      cudaError_t e = prof->record(st);
+      if (e != cudaSuccess) return e;
+      e = dispatch(a, epi);
+      if (e != cudaSuccess) return e;
+      return prof->record(st);
+    }
+    return dispatch(a, epi);
+  }
+  // q = Mhat p (needs u = B p already formed) ; t scratch (odd)
+  cudaError_t mhat(F<S> p, F<S> u, F<S> t, F<S> q, const int* active, double* partials) const {
+    F<S> none;
+    cudaError_t e = run(E_BAINV, 1, 0, u, none, none, T(0), T(1), t, active, nullptr);
+    if (e != cudaSuccess) return e;
+    return run(E_A_SAME, 0, 0, t, p, none, T(1), T(-0.25), q, active, partials);
+  }
+  // r = Mhat^+ v ; t scratch (odd)
+  cudaError_t mhat_dag(F<S> v, F<S> t, F<S> r, const int* active, double* partials) const {
+    F<S> none;
+    cudaError_t e = run(E_AINVD_BD, 1, 1, v, none, none, T(0), T(1), t, active, nullptr);
+    if (e != cudaSuccess) return e;
+    return run(E_AD_SAME_BD, 0, 1, t, v, none, T(1), T(-0.25), r, active, partials);
+  }
+};
+
+// Tiling of the fast hop kernels.  Storage types narrower than FP64 stage the
+// neighbour sites in shared memory when a block can hold whole sites (all N
+// slots of nsb sites, at most ~200 KB of staging); FP64 runs unstaged.
+// Hop kernel variants: 0 automatic, 1 CUDA-core direct loads, 2 CUDA-core staged, 3 tensor-core (fp16).
+enum { HOP_AUTO = 0, HOP_DIRECT = 1, HOP_STAGED = 2, HOP_MMA = 3 };
+
+template <typename S>
+Tiling fast_tiling(const Geom& g, int L5, int N, int nsb_req, bool* staged, bool allow_staging);
+
+// Tiling and kernel choice of a FastOp.
+template <typename S, typename T>
+void choose_hop(FastOp<S, T>& op, const Cfg* cfg, int nsb_req, int variant, const StageInfo* stage) {
+  const Geom& g = op.g;
+  const int L5 = op.L5, N = op.N, upb = L5 * N;
+  bool staged = false;
+  op.mma = false;
+  op.stage = nullptr;
+  op.U16 = cfg->U16;
+  if (variant == HOP_MMA && std::is_same<S, __half>::value && upb % 8 == 0 && upb <= 1024 && cfg->U16) {
+    int nsb = nsb_req > 0 ? nsb_req : (128 / upb > 1 ? 128 / upb : 1);
+    if (nsb > 64) nsb = 64;
+    while (nsb > 1 && nsb * upb > 1024) nsb--;
+    op.tl = make_tiling(g.Vh, L5, N, nsb, nsb * upb);
+    if (mma_hop_usable(op.tl, L5, N)) { op.mma = true; return; }
+  }
+  op.tl = fast_tiling<S>(g, L5, N, nsb_req, &staged, variant == HOP_STAGED);
+  op.stage = staged ? stage : nullptr;
+}
+
+template <typename S>
+Tiling fast_tiling(const Geom& g, int L5, int N, int nsb_req, bool* staged, bool allow_staging) {
+  using T = typename StoreTraits<S>::T;
+  int maxthr = fast_max_threads<S, T>();
+  if (maxthr > 1024) maxthr = 1024;
+  const int upb = L5 * N;
+  *staged = false;
+  if (allow_staging && !std::is_same<S, double>::value && upb <= maxthr) {
+    int nsb = nsb_req > 0 ? nsb_req : (128 / upb > 1 ? 128 / upb : 1);
+    if (nsb > 64) nsb = 64;
+    for (; nsb >= 1; nsb--) {
+      if (nsb * upb > maxthr) continue;
+      Tiling t = make_tiling(g.Vh, L5, N, nsb, nsb * upb);
+      if (t.rt == N && staged_smem_bytes<S, T>(t, L5, N) <= 110 * 1024) { *staged = true; return t; }
     }
   }
+  int smem_thr = (int)(200 * 1024 / (25 * sizeof(T)));
+  if (smem_thr < maxthr) maxthr = smem_thr;
+  int nsb = nsb_req > 0 ? nsb_req : 2;
+  if (nsb > 64) nsb = 64;
+  return make_tiling(g.Vh, L5, N, nsb, maxthr);
+}
+
+// Bound of device-side waits in clock cycles.
+long long wait_budget(int device, double seconds) {
+  int khz = 0;
+  if (cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, device) != cudaSuccess || khz <= 0) khz = 2000000;
+  return (long long)(seconds * 1e3 * (double)khz);
+}
+
+template <typename T>
+Fifth<T> make_fifth(const Action& act, const T* mass_dev) {
+  Fifth<T> f;
+  const double d = 4.0 - act.M5;
+  const double alpha = act.b5 * d + 1.0, beta = act.c5 * d - 1.0;
+  f.alpha = (T)alpha; f.beta = (T)beta; f.b5 = (T)act.b5; f.c5 = (T)act.c5;
+  f.inv_alpha = (T)(1.0 / alpha); f.kap = (T)(beta / alpha);
+  f.powL = (T)std::pow(-beta / alpha, act.L5);
+  f.mass = mass_dev;
+  return f;
+}
+
+// Named device buffers of a context, reused across calls (grown on demand).
+void* ws_get(mdwf_ctx* ctx, const std::string& name, size_t bytes, cudaError_t* err) {
+  auto& e = ctx->ws[name];
+  if (e.second < bytes) {
+    if (e.first) cudaFree(e.first);
+    e.first = nullptr;
+    e.second = 0;
+    *err = cudaMalloc(&e.first, bytes ? bytes : 16);
+    if (*err != cudaSuccess) return nullptr;
+    e.second = bytes;
+  }
+  return e.first;
+}
+
+template <typename S>
+cudaError_t ws_field(mdwf_ctx* ctx, const std::string& name, long units, F<S>* f) {
+  cudaError_t e = cudaSuccess;
+  f->v = (S*)ws_get(ctx, name + ".v", sizeof(S) * 24 * (size_t)units, &e);
+  if (e != cudaSuccess) return e;
+  f->n = nullptr;
+  if (StoreTraits<S>::kNorm) f->n = (float*)ws_get(ctx, name + ".n", sizeof(float) * (size_t)units, &e);
+  return e;
 }
 
 // ---------------------------------------------------------------------------
@@ -318,133 +538,212 @@ template <typename S>
 struct BatchSolver {
   using T = typename StoreTraits<S>::T;
   using SX = typename std::conditional<std::is_same<S, double>::value, double, float>::type;
+  static constexpr bool kFP64 = std::is_same<S, double>::value;
 
   mdwf_ctx* ctx;
   const Cfg* cfg;
   int N, L5;
-  Op<double, double> op64;
-  Op<S, T> opS;
-  Tiling tl_blas64, tl_blasS;
-  DevTables<double> M64;
-  DevTables<T> MS;
-  // FP64 fields: b (even, odd), x (even = x_hi, odd), bhat, rho64, u64 (even), t64 (odd)
-  FieldBuf<double> b_e, b_o, x_e, x_o, bhat, rho64, u64, t64;
-  // inner fields
-  FieldBuf<S> p, u, t, q, rho, r;
-  FieldBuf<SX> xlo;
-  DBuf partials, scal_d, scal_i, umask_d;
+  FastOp<double, double> op64;
+  FastOp<float, float> op32;
+  FastOp<S, T> opS;
+  Tiling tl_blas;
+  // FP64: sources, solution (x_acc + x_hi on even sites, x_o), reference residual bhat
+  F<double> b_e, b_o, x_acc, x_hi, x_o, bhat, rho64, u64, t64;
+  F<float> xf, uf, tf, qf;       // FP32 reliable updates
+  F<S> p, u, t, q, rho, r;       // inner vectors
+  F<SX> xlo;
+  double* part = nullptr;
+  double* mass64 = nullptr;
+  float* mass32 = nullptr;
   Scal sc;
+  int* umask_d = nullptr;
   cudaGraphExec_t graph = nullptr;
   int graph_iters = 0;
+  long long launches = 0, graph_launches = 0;
+  Prof prof;
+  bool profiling = false;
+  StageInfo stage;
+  int* errw = nullptr;            // device status word of the bounded waits
 
   ~BatchSolver() { if (graph) cudaGraphExecDestroy(graph); }
 
-  int init(mdwf_ctx* c, const Cfg* cf, const std::vector<double>& masses, int nsb, cudaStream_t st) {
+  int init(mdwf_ctx* c, const Cfg* cf, const std::vector<double>& masses, int nsb, bool profile,
+           const mdwf_solver_opts& o, cudaStream_t st) {
     mdwf_ctx* ctx = c;
     this->ctx = c;
     cfg = cf;
     N = (int)masses.size();
     L5 = cf->act.L5;
     const Geom& g = c->g;
-    op64.g = g; op64.L5 = L5; op64.N = N; op64.anti = cf->anti; op64.U = cf->U64; op64.st = st;
-    op64.tl = tiling_for<double>(g, L5, N, nsb, true);
-    opS.g = g; opS.L5 = L5; opS.N = N; opS.anti = cf->anti; opS.st = st;
-    opS.U = std::is_same<T, double>::value ? (const T*)cf->U64 : (const T*)cf->U32;
-    opS.tl = tiling_for<S>(g, L5, N, op64.tl.nsb, true);
-    tl_blas64 = make_tiling(g.Vh, L5, N, op64.tl.nsb, 1024);
-    tl_blasS = tl_blas64;
-    Tables tab;
-    tab.build(cf->act, masses);
-    CK(M64.upload(tab, st));
-    CK(MS.upload(tab, st));
     long units = g.Vh * L5 * N;
-    FieldBuf<double>* f64[] = {&b_e, &b_o, &x_e, &x_o, &bhat, &rho64, &u64, &t64};
-    for (auto* f : f64) CK(f->alloc(units));
-    FieldBuf<S>* fS[] = {&p, &u, &t, &q, &rho, &r};
-    for (auto* f : fS) CK(f->alloc(units));
-    CK(xlo.alloc(units));
-    // one partial per site covers every tiling (nsb >= 1)
-    CK(partials.alloc(sizeof(double) * g.Vh * N));
-    CK(scal_d.alloc(sizeof(double) * 10 * N));
-    CK(scal_i.alloc(sizeof(int) * 3 * N));
-    CK(umask_d.alloc(sizeof(int) * N));
-    double* d = scal_d.as<double>();
+    cudaError_t e = cudaSuccess;
+    mass64 = (double*)ws_get(c, "mass64", sizeof(double) * N, &e); CK(e);
+    mass32 = (float*)ws_get(c, "mass32", sizeof(float) * N, &e); CK(e);
+    std::vector<float> m32(masses.begin(), masses.end());
+    CK(cudaMemcpyAsync(mass64, masses.data(), sizeof(double) * N, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(mass32, m32.data(), sizeof(float) * N, cudaMemcpyHostToDevice, st));
+    op64.g = g; op64.L5 = L5; op64.N = N; op64.anti = cf->anti; op64.U = cf->U64; op64.st = st;
+    op64.f = make_fifth<double>(cf->act, mass64);
+    op32.g = g; op32.L5 = L5; op32.N = N; op32.anti = cf->anti; op32.U = cf->U32; op32.st = st;
+    op32.f = make_fifth<float>(cf->act, mass32);
+    opS.g = g; opS.L5 = L5; opS.N = N; opS.anti = cf->anti; opS.st = st;
+    opS.U = kFP64 ? (const T*)cf->U64 : (const T*)cf->U32;
+    opS.f = make_fifth<T>(cf->act, kFP64 ? (const T*)mass64 : (const T*)mass32);
+    if (nsb * L5 > 1024) nsb = 1;
+    tl_blas = make_tiling(g.Vh, L5, N, 2, kFP64 ? 512 : 1024);
+    errw = (int*)ws_get(c, "errw", sizeof(int), &e); CK(e);
+    CK(cudaMemsetAsync(errw, 0, sizeof(int), st));
+    stage.spin_bytes = stage.nrm_bytes = 0;
+    stage.budget = wait_budget(c->device, o.wait_timeout_s > 0 ? o.wait_timeout_s : 2.0);
+    stage.extra_tx = o.timeout_test ? 16u : 0u;
+    stage.err = errw;
+    // the wait-timeout test needs the staged kernel, whose waits it exercises
+    const int variant = o.timeout_test ? HOP_STAGED : o.hop_variant;
+    choose_hop(op64, cf, 0, HOP_DIRECT, &stage);
+    choose_hop(op32, cf, nsb, variant == HOP_AUTO ? HOP_DIRECT : variant, &stage);
+    choose_hop(opS, cf, nsb, variant, &stage);
+    op64.launches = op32.launches = opS.launches = &launches;
+    profiling = profile;
+    if (profile) opS.prof = &prof;
+    F<double>* f64[] = {&b_e, &b_o, &x_acc, &x_hi, &x_o, &bhat, &rho64, &u64, &t64};
+    const char* n64[] = {"b_e", "b_o", "x_acc", "x_hi", "x_o", "bhat", "rho64", "u64", "t64"};
+    for (int i = 0; i < 9; i++) CK(ws_field<double>(c, n64[i], units, f64[i]));
+    if (!kFP64) {
+      F<float>* f32[] = {&xf, &uf, &tf, &qf};
+      const char* n32[] = {"xf", "uf", "tf", "qf"};
+      for (int i = 0; i < 4; i++) CK(ws_field<float>(c, n32[i], units, f32[i]));
+    }
+    F<S>* fS[] = {&p, &u, &t, &q, &rho, &r};
+    const char* nS[] = {"p", "u", "t", "q", "rho", "r"};
+    for (int i = 0; i < 6; i++) CK(ws_field<S>(c, std::string("S.") + nS[i], units, fS[i]));
+    CK(ws_field<SX>(c, "xlo", units, &xlo));
+    part = (double*)ws_get(c, "partials", sizeof(double) * g.Vh * N, &e); CK(e);
+    double* d = (double*)ws_get(c, "scal_d", sizeof(double) * 11 * N, &e); CK(e);
+    int* ip = (int*)ws_get(c, "scal_i", sizeof(int) * 3 * N, &e); CK(e);
+    umask_d = (int*)ws_get(c, "umask", sizeof(int) * N, &e); CK(e);
     sc.gamma = d; sc.gamma_prev = d + N; sc.alpha = d + 2 * N; sc.beta = d + 3 * N; sc.rho2 = d + 4 * N;
     sc.rho2_max = d + 5 * N; sc.stop2 = d + 6 * N; sc.qq = d + 7 * N; sc.rr = d + 8 * N; sc.tmp = d + 9 * N;
-    int* ip = scal_i.as<int>();
+    sc.bhat2 = d + 10 * N;
     sc.active = ip; sc.flags = ip + N; sc.iters = ip + 2 * N;
-    CK(cudaMemsetAsync(scal_d.p, 0, scal_d.bytes, st));
-    CK(cudaMemsetAsync(scal_i.p, 0, scal_i.bytes, st));
-    CK(cudaMemsetAsync(x_e.v.p, 0, x_e.v.bytes, st));
-    CK(cudaMemsetAsync(xlo.v.p, 0, xlo.v.bytes, st));
-    for (auto* f : fS) { CK(cudaMemsetAsync(f->v.p, 0, f->v.bytes, st)); if (f->n.p) CK(cudaMemsetAsync(f->n.p, 0, f->n.bytes, st)); }
+    CK(cudaMemsetAsync(d, 0, sizeof(double) * 11 * N, st));
+    CK(cudaMemsetAsync(ip, 0, sizeof(int) * 3 * N, st));
+    const size_t b64 = sizeof(double) * 24 * (size_t)units;
+    CK(cudaMemsetAsync(x_acc.v, 0, b64, st));
+    CK(cudaMemsetAsync(x_hi.v, 0, b64, st));
+    CK(cudaMemsetAsync(xlo.v, 0, sizeof(SX) * 24 * (size_t)units, st));
+    CK(cudaMemsetAsync(p.v, 0, sizeof(S) * 24 * (size_t)units, st));
+    if (p.n) CK(cudaMemsetAsync(p.n, 0, sizeof(float) * (size_t)units, st));
     return MDWF_OK;
   }
 
-  // |field|^2 per slot into dst[N] (device).
   template <typename SS>
-  cudaError_t norms(F<SS> f, const Tiling& tl, const int* mask, double* dst) {
-    cudaError_t e = norm2_partials<SS>(f.v, f.n, tl, ctx->g.Vh, L5, N, mask, partials.as<double>(), op64.st);
+  cudaError_t norms(F<SS> f, const int* mask, double* dst) {
+    launches += 2;
+    cudaError_t e = norm2_partials<SS>(f.v, f.n, tl_blas, ctx->g.Vh, L5, N, mask, part, op64.st);
     if (e != cudaSuccess) return e;
-    return finalize(partials.as<double>(), tl.ntiles, N, dst, op64.st);
+    return finalize(part, ctx->g.Vh, N, dst, op64.st);
   }
 
-  // One CG iteration on all active slots (see file header).
+  // One CG iteration on all active slots.
   cudaError_t iteration() {
     const Geom& g = ctx->g;
     cudaStream_t st = op64.st;
-    double* part = partials.as<double>();
     cudaError_t e;
-    const int N_ = N;
-    e = xpay<S>(r.f().v, r.f().n, p.f().v, p.f().n, sc.beta, tl_blasS, g.Vh, L5, N_, sc.active, st);
+    launches += 8;  // xpay_b, axpy, 3 finalize, 3 scalar kernels (+ 4 hops counted in FastOp::run)
+    e = xpay_b<S>(r.v, r.n, p.v, p.n, u.v, u.n, sc.beta, opS.f, tl_blas, g.Vh, L5, N, sc.active, st);
     if (e != cudaSuccess) return e;
-    e = opS.schur(0, p.f(), u.f(), t.f(), q.f(), MS, sc.active, part);
+    e = opS.mhat(p, u, t, q, sc.active, part);
     if (e != cudaSuccess) return e;
-    e = finalize(part, opS.tl.ntiles, N_, sc.qq, st);
+    e = finalize(part, g.Vh, N, sc.qq, st);
     if (e != cudaSuccess) return e;
-    k_alpha<<<1, 1024, 0, st>>>(sc, N_);
-    e = axpy_x_rho<SX, S>(xlo.f().v, p.f().v, p.f().n, rho.f().v, rho.f().n, q.f().v, q.f().n, sc.alpha, tl_blasS,
-                          g.Vh, L5, N_, sc.active, part, st);
+    k_alpha<<<1, 1024, 0, st>>>(sc, N);
+    e = axpy_x_rho<SX, S>(xlo.v, p.v, p.n, rho.v, rho.n, q.v, q.n, sc.alpha, tl_blas, g.Vh, L5, N, sc.active, part, st);
     if (e != cudaSuccess) return e;
-    e = finalize(part, tl_blasS.ntiles, N_, sc.tmp, st);
+    e = finalize(part, g.Vh, N, sc.tmp, st);
     if (e != cudaSuccess) return e;
-    k_after_rho<<<1, 1024, 0, st>>>(sc, N_);
-    e = opS.schur(1, rho.f(), u.f(), t.f(), r.f(), MS, sc.active, part);
+    k_after_rho<<<1, 1024, 0, st>>>(sc, N);
+    e = opS.mhat_dag(rho, t, r, sc.active, part);
     if (e != cudaSuccess) return e;
-    e = finalize(part, opS.tl.ntiles, N_, sc.rr, st);
+    e = finalize(part, g.Vh, N, sc.rr, st);
     if (e != cudaSuccess) return e;
-    k_beta<<<1, 1024, 0, st>>>(sc, N_);
+    k_beta<<<1, 1024, 0, st>>>(sc, N);
     return cudaGetLastError();
   }
 
-  // FP64 residual recomputation for the slots in umask (device).
-  int* umask() { return umask_d.as<int>(); }
+  // r = Mhat^+ rho and |r|^2 for the slots in um.
+  cudaError_t normal_residual(const int* um) {
+    launches += 1;
+    cudaError_t e = opS.mhat_dag(rho, t, r, um, part);
+    if (e != cudaSuccess) return e;
+    return finalize(part, ctx->g.Vh, N, sc.rr, op64.st);
+  }
 
-  cudaError_t reliable_update(const int* um) {
+  // Reliable update with FP32 arithmetic: rho = bhat - Mhat x_hi (FP64 difference).
+  cudaError_t update32(const int* um) {
     const Geom& g = ctx->g;
     cudaStream_t st = op64.st;
-    double* part = partials.as<double>();
-    cudaError_t e = accum_xhi<SX>(x_e.f().v, xlo.f().v, tl_blas64, g.Vh, L5, N, um, st);
+    cudaError_t e;
+    launches += 6;  // accum, convert, bop, resid_update, finalize, scalar kernel
+    e = accum_xhi<SX>(x_hi.v, xlo.v, tl_blas, g.Vh, L5, N, um, st);
     if (e != cudaSuccess) return e;
-    F<double> none;
-    // rho64 = bhat - A x + 1/4 H_eo B A^-1 H_oe B x
-    e = op64.run(false, 0, 0, x_e.f(), none, M64[MK_B], none, nullptr, 0.0, u64.f(), um, nullptr);
+    e = convert<double, float>(x_hi.v, nullptr, xf.v, nullptr, tl_blas, g.Vh, L5, N, um, st);
     if (e != cudaSuccess) return e;
-    e = op64.run(true, 1, 0, u64.f(), none, nullptr, none, M64[MK_BAinv], 1.0, t64.f(), um, nullptr);
+    e = bop<float>(xf.v, nullptr, uf.v, nullptr, op32.f, tl_blas, g.Vh, L5, N, um, st);
     if (e != cudaSuccess) return e;
-    e = op64.run(true, 0, 0, t64.f(), x_e.f(), M64[MK_negA], bhat.f(), nullptr, 0.25, rho64.f(), um, part);
+    e = op32.mhat(xf, uf, tf, qf, um, nullptr);
     if (e != cudaSuccess) return e;
-    e = finalize(part, op64.tl.ntiles, N, sc.tmp, st);
+    e = resid_update<S>(bhat.v, qf.v, rho.v, rho.n, tl_blas, g.Vh, L5, N, um, part, st);
     if (e != cudaSuccess) return e;
-    e = convert<double, S>(rho64.f().v, nullptr, rho.f().v, rho.f().n, tl_blas64, g.Vh, L5, N,
-                           um, st);
+    e = finalize(part, g.Vh, N, sc.tmp, st);
     if (e != cudaSuccess) return e;
-    e = opS.schur(1, rho.f(), u.f(), t.f(), r.f(), MS, um, part);
-    if (e != cudaSuccess) return e;
-    e = finalize(part, opS.tl.ntiles, N, sc.rr, st);
+    e = normal_residual(um);
     if (e != cudaSuccess) return e;
     k_after_update<<<1, 1024, 0, st>>>(sc, N, um);
     return cudaGetLastError();
+  }
+
+  // FP64 re-reference: rho = bhat - Mhat x_hi in FP64, then bhat <- rho and
+  // x_acc += x_hi, x_hi = 0.  With zero_x the operator is skipped (x_hi = 0).
+  cudaError_t reref(const int* um, bool zero_x) {
+    const Geom& g = ctx->g;
+    cudaStream_t st = op64.st;
+    cudaError_t e;
+    F<double> none;
+    if (zero_x) {
+      launches += 1;
+      e = convert<double, double>(bhat.v, nullptr, rho64.v, nullptr, tl_blas, g.Vh, L5, N, um, st);
+      if (e != cudaSuccess) return e;
+    } else {
+      launches += 2;
+      e = accum_xhi<SX>(x_hi.v, xlo.v, tl_blas, g.Vh, L5, N, um, st);
+      if (e != cudaSuccess) return e;
+      e = bop<double>(x_hi.v, nullptr, u64.v, nullptr, op64.f, tl_blas, g.Vh, L5, N, um, st);
+      if (e != cudaSuccess) return e;
+      e = op64.run(E_BAINV, 1, 0, u64, none, none, 0.0, 1.0, t64, um, nullptr);
+      if (e != cudaSuccess) return e;
+      e = op64.run(E_A_SAME, 0, 0, t64, x_hi, bhat, -1.0, 0.25, rho64, um, nullptr);
+      if (e != cudaSuccess) return e;
+    }
+    e = norms<double>(rho64, um, sc.tmp);
+    if (e != cudaSuccess) return e;
+    launches += 4;  // copy, accum, convert, scalar kernel
+    e = convert<double, double>(rho64.v, nullptr, bhat.v, nullptr, tl_blas, g.Vh, L5, N, um, st);
+    if (e != cudaSuccess) return e;
+    e = accum_xhi<double>(x_acc.v, x_hi.v, tl_blas, g.Vh, L5, N, um, st);
+    if (e != cudaSuccess) return e;
+    e = convert<double, S>(rho64.v, nullptr, rho.v, rho.n, tl_blas, g.Vh, L5, N, um, st);
+    if (e != cudaSuccess) return e;
+    e = normal_residual(um);
+    if (e != cudaSuccess) return e;
+    k_after_reref<<<1, 1024, 0, st>>>(sc, N, um);
+    return cudaGetLastError();
+  }
+
+  cudaError_t collect(bool after_graph) {
+    if (!profiling) return cudaSuccess;
+    cudaError_t e = prof.collect();
+    if (e != cudaSuccess || !after_graph) return e;
+    return prof.collect_graph();
   }
 
   int run_chunk(int k, bool use_graph) {
@@ -457,10 +756,16 @@ struct BatchSolver {
     if (graph == nullptr || graph_iters != k) {
       if (graph) { cudaGraphExecDestroy(graph); graph = nullptr; }
       cudaGraph_t gr;
+      const long long c0 = launches;
+      prof.gused = 0;
+      prof.capturing = profiling;
       CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
       cudaError_t err = cudaSuccess;
       for (int i = 0; i < k && err == cudaSuccess; i++) err = iteration();
       cudaError_t e2 = cudaStreamEndCapture(st, &gr);
+      prof.capturing = false;
+      graph_launches = launches - c0;
+      launches = c0;
       CK(err);
       CK(e2);
       cudaError_t e3 = cudaGraphInstantiate(&graph, gr, 0);
@@ -469,6 +774,7 @@ struct BatchSolver {
       graph_iters = k;
     }
     CK(cudaGraphLaunch(graph, st));
+    launches += graph_launches;
     return MDWF_OK;
   }
 };
@@ -491,21 +797,21 @@ int solve_batch_impl(mdwf_ctx* ctx, Cfg* cfg, int n, const double* const* srcs, 
                      cudaStream_t st) {
   auto t0 = std::chrono::steady_clock::now();
   BatchSolver<S> sv;
-  int rc = sv.init(ctx, cfg, masses, o.nsb > 0 ? o.nsb : 2, st);
+  int rc = sv.init(ctx, cfg, masses, o.nsb, o.profile != 0, o, st);
   if (rc != MDWF_OK) return rc;
   const Geom& g = ctx->g;
   const int N = n, L5 = cfg->act.L5;
-  // pack sources
+  F<double> none;
+  sv.launches += 2 * N;
   for (int i = 0; i < N; i++) {
-    CK(pack_rhs<double>(srcs[i], sv.b_e.f().v, nullptr, g, L5, N, 0, i, st));
-    CK(pack_rhs<double>(srcs[i], sv.b_o.f().v, nullptr, g, L5, N, 1, i, st));
+    CK(pack_rhs<double>(srcs[i], sv.b_e.v, nullptr, g, L5, N, 0, i, st));
+    CK(pack_rhs<double>(srcs[i], sv.b_o.v, nullptr, g, L5, N, 1, i, st));
   }
-  // |b|^2 = |b_e|^2 + |b_o|^2 per slot
   std::vector<double> bb(N), bo(N);
   double* tmp = sv.sc.tmp;
-  CK(sv.norms(sv.b_e.f(), sv.tl_blas64, nullptr, tmp));
+  CK(sv.norms(sv.b_e, nullptr, tmp));
   CK(cudaMemcpyAsync(bb.data(), tmp, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
-  CK(sv.norms(sv.b_o.f(), sv.tl_blas64, nullptr, tmp));
+  CK(sv.norms(sv.b_o, nullptr, tmp));
   CK(cudaMemcpyAsync(bo.data(), tmp, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   std::vector<double> stop2(N);
@@ -517,49 +823,84 @@ int solve_batch_impl(mdwf_ctx* ctx, Cfg* cfg, int n, const double* const* srcs, 
     if (b2 == 0.0) act[i] = 0;
   }
   CK(cudaMemcpyAsync(sv.sc.stop2, stop2.data(), sizeof(double) * N, cudaMemcpyHostToDevice, st));
-  sv.sc.delta2 = o.delta * o.delta;
-  // bhat_e = b_e + 1/2 H_eo B A^-1 b_o
-  F<double> none;
-  CK(sv.op64.run(false, 1, 0, sv.b_o.f(), none, sv.M64[MK_BAinv], none, nullptr, 0.0, sv.t64.f(), nullptr, nullptr));
-  CK(sv.op64.run(true, 0, 0, sv.t64.f(), none, nullptr, sv.b_e.f(), nullptr, 0.5, sv.bhat.f(), nullptr, nullptr));
-  // initial residual (x = 0): a reliable update on every slot
+  sv.sc.delta2 = BatchSolver<S>::kFP64 ? 0.0 : o.delta * o.delta;
+  sv.sc.tau2 = BatchSolver<S>::kFP64 ? 0.0 : 1e-10;
+  // bhat_e = b_e + 1/2 H_eo B A^-1 b_o   (B A^-1 on the odd sites with the dense table kernel)
+  {
+    Op<double, double> loc;
+    loc.g = g; loc.L5 = L5; loc.N = N; loc.anti = cfg->anti; loc.U = cfg->U64; loc.st = st;
+    loc.tl = tiling_for<double>(g, L5, N, sv.op64.tl.nsb, true);
+    loc.launches = &sv.launches;
+    Tables tab;
+    tab.build(cfg->act, masses);
+    DevTables<double> M;
+    CK(M.upload(tab, st));
+    CK(loc.run(false, 1, 0, sv.b_o, none, M[MK_BAinv], none, nullptr, 0.0, sv.t64, nullptr, nullptr));
+    CK(sv.op64.run(E_RAW, 0, 0, sv.t64, none, sv.b_e, 0.0, 0.5, sv.bhat, nullptr, nullptr));
+  }
+  // initial residual (x = 0)
   std::vector<int> um(N);
   for (int i = 0; i < N; i++) um[i] = act[i];
   CK(cudaMemcpyAsync(sv.sc.active, act.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(sv.umask_d.p, um.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
-  CK(sv.reliable_update(sv.umask()));
-  std::vector<int> flags(N), iters(N), nupd(N, 1);
-  std::vector<int> done(N, 0);
+  CK(cudaMemcpyAsync(sv.umask_d, um.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
+  CK(sv.reref(sv.umask_d, true));
+  std::vector<int> flags(N), iters(N), nupd(N, 1), done(N, 0);
   for (int i = 0; i < N; i++) if (!act[i]) done[i] = 1;
   const int chunk = o.chunk > 0 ? o.chunk : 16;
+  auto read_flags = [&]() -> int {
+    int herr = 0;
+    CK(cudaMemcpyAsync(flags.data(), sv.sc.flags, sizeof(int) * N, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(iters.data(), sv.sc.iters, sizeof(int) * N, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&herr, sv.errw, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (herr) {
+      cudaMemsetAsync(sv.errw, 0, sizeof(int), st);
+      cudaStreamSynchronize(st);
+      return fail(ctx, MDWF_ERR_TIMEOUT, "a bounded device wait ran out (staged neighbour copies did not arrive)");
+    }
+    return MDWF_OK;
+  };
   for (;;) {
     bool all = true;
     for (int i = 0; i < N; i++) all = all && done[i];
     if (all) break;
     rc = sv.run_chunk(chunk, o.use_graph != 0);
     if (rc != MDWF_OK) return rc;
-    CK(cudaMemcpyAsync(flags.data(), sv.sc.flags, sizeof(int) * N, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(iters.data(), sv.sc.iters, sizeof(int) * N, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
+    if ((rc = read_flags())) return rc;
+    CK(sv.collect(o.use_graph != 0));
+    // reliable updates: FP32 arithmetic (mixed) or FP64 (FP64 solver)
     bool any = false;
     for (int i = 0; i < N; i++) {
       um[i] = (!done[i] && (flags[i] & (FLAG_INNER_DONE | FLAG_UPDATE))) ? 1 : 0;
       any = any || um[i];
     }
     if (any) {
-      CK(cudaMemcpyAsync(sv.umask_d.p, um.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
-      CK(sv.reliable_update(sv.umask()));
-      CK(cudaMemcpyAsync(flags.data(), sv.sc.flags, sizeof(int) * N, cudaMemcpyDeviceToHost, st));
-      CK(cudaStreamSynchronize(st));
+      CK(cudaMemcpyAsync(sv.umask_d, um.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
+      if (BatchSolver<S>::kFP64) CK(sv.reref(sv.umask_d, false));
+      else CK(sv.update32(sv.umask_d));
+      if ((rc = read_flags())) return rc;
+      CK(sv.collect(false));
+      for (int i = 0; i < N; i++) if (um[i]) nupd[i]++;
+    }
+    // FP64 re-references requested by the FP32 updates
+    any = false;
+    for (int i = 0; i < N; i++) {
+      um[i] = (!done[i] && (flags[i] & FLAG_REREF)) ? 1 : 0;
+      any = any || um[i];
+    }
+    if (any) {
+      CK(cudaMemcpyAsync(sv.umask_d, um.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
+      CK(sv.reref(sv.umask_d, false));
+      if ((rc = read_flags())) return rc;
+      CK(sv.collect(false));
       for (int i = 0; i < N; i++) if (um[i]) nupd[i]++;
     }
     bool stop_any = false;
     for (int i = 0; i < N; i++) {
       if (flags[i] & FLAG_DONE) done[i] = 1;
-      if (!done[i] && iters[i] >= o.max_iter) { done[i] = 1; act[i] = 0; stop_any = true; }
+      if (!done[i] && iters[i] >= o.max_iter) { done[i] = 1; stop_any = true; }
     }
     if (stop_any) {
-      // freeze slots that hit max_iter
       std::vector<int> a(N);
       CK(cudaMemcpyAsync(a.data(), sv.sc.active, sizeof(int) * N, cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
@@ -567,28 +908,27 @@ int solve_batch_impl(mdwf_ctx* ctx, Cfg* cfg, int n, const double* const* srcs, 
       CK(cudaMemcpyAsync(sv.sc.active, a.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
     }
   }
-  // x_hi += x_lo for everything not yet accumulated
-  CK(accum_xhi<typename BatchSolver<S>::SX>(sv.x_e.f().v, sv.xlo.f().v, sv.tl_blas64, g.Vh, L5, N, nullptr, st));
-  // x_o = A^-1 b_o + 1/2 A^-1 H_oe B x_e
-  CK(sv.op64.run(false, 0, 0, sv.x_e.f(), none, sv.M64[MK_B], none, nullptr, 0.0, sv.u64.f(), nullptr, nullptr));
-  CK(sv.op64.run(true, 1, 0, sv.u64.f(), sv.b_o.f(), sv.M64[MK_Ainv], none, sv.M64[MK_Ainv], 0.5, sv.x_o.f(),
-                 nullptr, nullptr));
-  // true residual r = b - D x on both parities: b - A x + 1/2 H B x
-  CK(sv.op64.run(false, 1, 0, sv.x_o.f(), none, sv.M64[MK_B], none, nullptr, 0.0, sv.t64.f(), nullptr, nullptr));
-  CK(sv.op64.run(true, 0, 0, sv.t64.f(), sv.x_e.f(), sv.M64[MK_negA], sv.b_e.f(), nullptr, 0.5, sv.rho64.f(),
-                 nullptr, nullptr));
+  // x_e = x_acc + x_hi + x_lo
+  sv.launches += 2 + 2 * N;
+  CK(accum_xhi<typename BatchSolver<S>::SX>(sv.x_hi.v, sv.xlo.v, sv.tl_blas, g.Vh, L5, N, nullptr, st));
+  CK(accum_xhi<double>(sv.x_acc.v, sv.x_hi.v, sv.tl_blas, g.Vh, L5, N, nullptr, st));
+  // x_o = A^-1 (b_o + 1/2 H_oe B x_e)
+  sv.launches += 2;
+  CK(bop<double>(sv.x_acc.v, nullptr, sv.u64.v, nullptr, sv.op64.f, sv.tl_blas, g.Vh, L5, N, nullptr, st));
+  CK(sv.op64.run(E_AINV_SAME, 1, 0, sv.u64, sv.b_o, none, 0.0, 0.5, sv.x_o, nullptr, nullptr));
+  // true residual b - D x = b - A x + 1/2 H B x on both parities
+  CK(bop<double>(sv.x_o.v, nullptr, sv.t64.v, nullptr, sv.op64.f, sv.tl_blas, g.Vh, L5, N, nullptr, st));
+  CK(sv.op64.run(E_A_SAME, 0, 0, sv.t64, sv.x_acc, sv.b_e, -1.0, 0.5, sv.rho64, nullptr, nullptr));
   std::vector<double> re(N), ro(N);
-  CK(sv.norms(sv.rho64.f(), sv.tl_blas64, nullptr, tmp));
+  CK(sv.norms(sv.rho64, nullptr, tmp));
   CK(cudaMemcpyAsync(re.data(), tmp, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
-  // odd part, reusing u64 (B x_e) and rho64 as scratch
-  CK(sv.op64.run(true, 1, 0, sv.u64.f(), sv.x_o.f(), sv.M64[MK_negA], sv.b_o.f(), nullptr, 0.5, sv.rho64.f(),
-                 nullptr, nullptr));
-  CK(sv.norms(sv.rho64.f(), sv.tl_blas64, nullptr, tmp));
+  CK(sv.op64.run(E_A_SAME, 1, 0, sv.u64, sv.x_o, sv.b_o, -1.0, 0.5, sv.rho64, nullptr, nullptr));
+  CK(sv.norms(sv.rho64, nullptr, tmp));
   CK(cudaMemcpyAsync(ro.data(), tmp, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(iters.data(), sv.sc.iters, sizeof(int) * N, cudaMemcpyDeviceToHost, st));
   for (int i = 0; i < N; i++) {
-    CK(unpack_rhs<double>(sv.x_e.f().v, nullptr, xs[i], g, L5, N, 0, i, st));
-    CK(unpack_rhs<double>(sv.x_o.f().v, nullptr, xs[i], g, L5, N, 1, i, st));
+    CK(unpack_rhs<double>(sv.x_acc.v, nullptr, xs[i], g, L5, N, 0, i, st));
+    CK(unpack_rhs<double>(sv.x_o.v, nullptr, xs[i], g, L5, N, 1, i, st));
   }
   CK(cudaStreamSynchronize(st));
   double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -604,6 +944,10 @@ int solve_batch_impl(mdwf_ctx* ctx, Cfg* cfg, int n, const double* const* srcs, 
       stats[i].converged = conv ? 1 : 0;
       stats[i].rel_true_resid = rel;
       stats[i].time_s = secs;
+      stats[i].hop_launches = (int)sv.prof.n;
+      stats[i].hop_ms = sv.prof.ms;
+      stats[i].kernel_launches = sv.launches;
+      stats[i].hop_units = (long long)g.Vh * L5 * N;
     }
   }
   if (status != MDWF_OK) fail(ctx, status, "solve did not reach the tolerance within max_iter");
@@ -667,19 +1011,27 @@ int apply_dev(mdwf_ctx* ctx, Cfg* cfg, int kind, int arg1, int arg2, const doubl
   CK(cudaMemsetAsync(oe.v.p, 0, oe.v.bytes, st));
   CK(cudaMemsetAsync(oo.v.p, 0, oo.v.bytes, st));
   F<double> none;
+  DBuf mass;
+  CK(mass.alloc(sizeof(double)));
+  CK(cudaMemcpyAsync(mass.p, &cfg->act.mf, sizeof(double), cudaMemcpyHostToDevice, st));
+  FastOp<double, double> fo;
+  fo.g = g; fo.L5 = L5; fo.N = 1; fo.anti = cfg->anti; fo.U = cfg->U64; fo.st = st;
+  fo.f = make_fifth<double>(cfg->act, mass.as<double>());
+  choose_hop(fo, cfg, 0, HOP_DIRECT, nullptr);
+  Tiling tb = make_tiling(g.Vh, L5, 1, 2, 512);
   if (kind == 0) {
     int par = arg1, dag = arg2;
-    if (par == 0 || par == -1) CK(op.run(true, 0, dag, io.f(), none, nullptr, none, nullptr, 1.0, oe.f(), nullptr, nullptr));
-    if (par == 1 || par == -1) CK(op.run(true, 1, dag, ie.f(), none, nullptr, none, nullptr, 1.0, oo.f(), nullptr, nullptr));
+    if (par == 0 || par == -1) CK(fo.run(E_RAW, 0, dag, io.f(), none, none, 0.0, 1.0, oe.f(), nullptr, nullptr));
+    if (par == 1 || par == -1) CK(fo.run(E_RAW, 1, dag, ie.f(), none, none, 0.0, 1.0, oo.f(), nullptr, nullptr));
   } else if (kind == 1) {
     if (!arg1) {  // D x = A x - 1/2 H B x
-      CK(op.run(false, 0, 0, ie.f(), none, M[MK_B], none, nullptr, 0.0, te.f(), nullptr, nullptr));
-      CK(op.run(false, 1, 0, io.f(), none, M[MK_B], none, nullptr, 0.0, to.f(), nullptr, nullptr));
-      CK(op.run(true, 0, 0, to.f(), ie.f(), M[MK_A], none, nullptr, -0.5, oe.f(), nullptr, nullptr));
-      CK(op.run(true, 1, 0, te.f(), io.f(), M[MK_A], none, nullptr, -0.5, oo.f(), nullptr, nullptr));
+      CK(bop<double>(ie.f().v, nullptr, te.f().v, nullptr, fo.f, tb, g.Vh, L5, 1, nullptr, st));
+      CK(bop<double>(io.f().v, nullptr, to.f().v, nullptr, fo.f, tb, g.Vh, L5, 1, nullptr, st));
+      CK(fo.run(E_A_SAME, 0, 0, to.f(), ie.f(), none, 1.0, -0.5, oe.f(), nullptr, nullptr));
+      CK(fo.run(E_A_SAME, 1, 0, te.f(), io.f(), none, 1.0, -0.5, oo.f(), nullptr, nullptr));
     } else {      // D^+ x = A^+ x - 1/2 B^+ H^+ x
-      CK(op.run(true, 0, 1, io.f(), ie.f(), M[MK_Ad], none, M[MK_Bd], -0.5, oe.f(), nullptr, nullptr));
-      CK(op.run(true, 1, 1, ie.f(), io.f(), M[MK_Ad], none, M[MK_Bd], -0.5, oo.f(), nullptr, nullptr));
+      CK(fo.run(E_AD_SAME_BD, 0, 1, io.f(), ie.f(), none, 1.0, -0.5, oe.f(), nullptr, nullptr));
+      CK(fo.run(E_AD_SAME_BD, 1, 1, ie.f(), io.f(), none, 1.0, -0.5, oo.f(), nullptr, nullptr));
     }
   } else if (kind == 2) {
     static const int kinds[3][2] = {{MK_A, MK_Ad}, {MK_B, MK_Bd}, {MK_Ainv, MK_Ainvd}};
@@ -709,26 +1061,94 @@ int schur_apply_impl(mdwf_ctx* ctx, Cfg* cfg, const double* in_dev, double* out_
   using T = typename StoreTraits<S>::T;
   const Geom& g = ctx->g;
   const int L5 = cfg->act.L5;
-  Op<S, T> op;
+  DBuf mass;
+  CK(mass.alloc(sizeof(T)));
+  const T m = (T)cfg->act.mf;
+  CK(cudaMemcpyAsync(mass.p, &m, sizeof(T), cudaMemcpyHostToDevice, st));
+  FastOp<S, T> op;
   op.g = g; op.L5 = L5; op.N = 1; op.anti = cfg->anti; op.st = st;
   op.U = std::is_same<T, double>::value ? (const T*)cfg->U64 : (const T*)cfg->U32;
-  op.tl = tiling_for<S>(g, L5, 1, 2, true);
-  Tables tab;
-  tab.build(cfg->act, std::vector<double>(1, cfg->act.mf));
-  DevTables<T> M;
-  CK(M.upload(tab, st));
+  op.f = make_fifth<T>(cfg->act, mass.as<T>());
+  DBuf errw;
+  CK(errw.alloc(sizeof(int)));
+  CK(cudaMemsetAsync(errw.p, 0, sizeof(int), st));
+  StageInfo si;
+  si.spin_bytes = si.nrm_bytes = 0;
+  si.budget = wait_budget(ctx->device, 2.0);
+  si.extra_tx = 0;
+  si.err = errw.as<int>();
+  choose_hop(op, cfg, 0, HOP_AUTO, &si);
+  Tiling tb = make_tiling(g.Vh, L5, 1, 2, 512);
   long units = g.Vh * L5;
   FieldBuf<S> in, u, t, out;
   for (auto* f : {&in, &u, &t, &out}) CK(f->alloc(units));
   FieldBuf<double> o64;
   CK(o64.alloc(2 * units));
   CK(pack_rhs<S>(in_dev, in.f().v, in.f().n, g, L5, 1, 0, 0, st));
-  CK(op.schur(dagger, in.f(), u.f(), t.f(), out.f(), M, nullptr, nullptr));
+  if (!dagger) {
+    CK(bop<S>(in.f().v, in.f().n, u.f().v, u.f().n, op.f, tb, g.Vh, L5, 1, nullptr, st));
+    CK(op.mhat(in.f(), u.f(), t.f(), out.f(), nullptr, nullptr));
+  } else {
+    CK(op.mhat_dag(in.f(), t.f(), out.f(), nullptr, nullptr));
+  }
   CK(unpack_rhs<S>(out.f().v, out.f().n, out_dev, g, L5, 1, 0, 0, st));
-  // zero odd sites of out: unpack a zero field into parity 1
   CK(cudaMemsetAsync(o64.v.p, 0, o64.v.bytes, st));
   CK(unpack_rhs<double>(o64.f().v, nullptr, out_dev, g, L5, 1, 1, 0, st));
+  int herr = 0;
+  CK(cudaMemcpyAsync(&herr, errw.p, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  if (herr) return fail(ctx, MDWF_ERR_TIMEOUT, "a bounded device wait ran out");
+  return MDWF_OK;
+}
+
+// Batched Schur operator on device API-layout fields (the solver's hot kernels).
+template <typename S>
+int schur_batch_impl(mdwf_ctx* ctx, Cfg* cfg, int n, const double* const* in, double* const* out,
+                     const std::vector<double>& masses, int dagger, int flags, cudaStream_t st) {
+  using T = typename StoreTraits<S>::T;
+  const Geom& g = ctx->g;
+  const int L5 = cfg->act.L5, N = n;
+  const long units = g.Vh * L5 * N;
+  cudaError_t e = cudaSuccess;
+  T* mass = (T*)ws_get(ctx, "sb.mass", sizeof(T) * N, &e); CK(e);
+  std::vector<T> mh(masses.begin(), masses.end());
+  CK(cudaMemcpyAsync(mass, mh.data(), sizeof(T) * N, cudaMemcpyHostToDevice, st));
+  int* errw = (int*)ws_get(ctx, "sb.errw", sizeof(int), &e); CK(e);
+  CK(cudaMemsetAsync(errw, 0, sizeof(int), st));
+  FastOp<S, T> op;
+  op.g = g; op.L5 = L5; op.N = N; op.anti = cfg->anti; op.st = st;
+  op.U = std::is_same<T, double>::value ? (const T*)cfg->U64 : (const T*)cfg->U32;
+  op.f = make_fifth<T>(cfg->act, mass);
+  StageInfo si;
+  si.spin_bytes = si.nrm_bytes = 0;
+  si.budget = wait_budget(ctx->device, 2.0);
+  si.extra_tx = 0;
+  si.err = errw;
+  choose_hop(op, cfg, 0, flags, &si);
+  Tiling tb = make_tiling(g.Vh, L5, N, 2, 1024);
+  F<S> fin, fu, ft, fo;
+  CK(ws_field<S>(ctx, "sb.in", units, &fin));
+  CK(ws_field<S>(ctx, "sb.u", units, &fu));
+  CK(ws_field<S>(ctx, "sb.t", units, &ft));
+  CK(ws_field<S>(ctx, "sb.out", units, &fo));
+  F<double> zero;
+  CK(ws_field<double>(ctx, "sb.zero", g.Vh * L5, &zero));
+  CK(cudaMemsetAsync(zero.v, 0, sizeof(double) * 24 * (size_t)g.Vh * L5, st));
+  for (int i = 0; i < N; i++) CK(pack_rhs<S>(in[i], fin.v, fin.n, g, L5, N, 0, i, st));
+  if (!dagger) {
+    CK(bop<S>(fin.v, fin.n, fu.v, fu.n, op.f, tb, g.Vh, L5, N, nullptr, st));
+    CK(op.mhat(fin, fu, ft, fo, nullptr, nullptr));
+  } else {
+    CK(op.mhat_dag(fin, ft, fo, nullptr, nullptr));
+  }
+  for (int i = 0; i < N; i++) {
+    CK(unpack_rhs<S>(fo.v, fo.n, out[i], g, L5, N, 0, i, st));
+    CK(unpack_rhs<double>(zero.v, nullptr, out[i], g, L5, 1, 1, 0, st));
+  }
+  int herr = 0;
+  CK(cudaMemcpyAsync(&herr, errw, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (herr) return fail(ctx, MDWF_ERR_TIMEOUT, "a bounded device wait ran out");
   return MDWF_OK;
 }
 
@@ -777,7 +1197,9 @@ void mdwf_default_opts(mdwf_solver_opts* o) {
   o->delta = 0.1;
   o->chunk = 16;
   o->use_graph = 1;
-  o->nsb = 2;
+  o->nsb = 0;
+  o->wait_timeout_s = 2.0;
+  o->hop_variant = 0;
 }
 
 int mdwf_create(const int dims[4], int device, mdwf_ctx** out) {
@@ -802,7 +1224,10 @@ int mdwf_destroy(mdwf_ctx* ctx) {
   for (auto& kv : ctx->cfgs) {
     if (kv.second.U64) cudaFree(kv.second.U64);
     if (kv.second.U32) cudaFree(kv.second.U32);
+    if (kv.second.U16) cudaFree(kv.second.U16);
   }
+  for (auto& kv : ctx->ws)
+    if (kv.second.first) cudaFree(kv.second.first);
   cudaStreamDestroy(ctx->stream);
   delete ctx;
   return MDWF_OK;
@@ -816,9 +1241,12 @@ int mdwf_load_gauge(mdwf_ctx* ctx, int cfg_id, const double* U, int t_antiperiod
   const Geom& g = ctx->g;
   const size_t n = (size_t)g.V * 4 * 18;
   if (!all_finite(U, n)) return fail(ctx, MDWF_ERR_NONFINITE, "gauge field has NaN/Inf");
-  // reorder to [parity][h][mu][18]
+  // reorder to [parity][h][mu][18] (FP64) and [parity][h][mu][20] (FP32, padded)
+  const size_t n32 = (size_t)g.V * 4 * kLinkStride32;
+  const size_t n16 = (size_t)g.V * 4 * 9;
   std::vector<double> h64(n);
-  std::vector<float> h32(n);
+  std::vector<float> h32(n32, 0.0f);
+  std::vector<__half2> h16(n16);
   for (long lex = 0; lex < g.V; lex++) {
     long r = lex;
     int c[4];
@@ -828,17 +1256,20 @@ int mdwf_load_gauge(mdwf_ctx* ctx, int cfg_id, const double* U, int t_antiperiod
     for (int mu = 0; mu < 4; mu++)
       for (int k = 0; k < 18; k++) {
         double v = U[(lex * 4 + mu) * 18 + k];
-        size_t dst = (((size_t)par * g.Vh + h) * 4 + mu) * 18 + k;
-        h64[dst] = v;
-        h32[dst] = (float)v;
+        size_t link = ((size_t)par * g.Vh + h) * 4 + mu;
+        h64[link * 18 + k] = v;
+        h32[link * kLinkStride32 + k] = (float)v;
+        if (k & 1) h16[link * 9 + k / 2] = __floats2half2_rn((float)U[(lex * 4 + mu) * 18 + k - 1], (float)v);
       }
   }
   CK(cudaSetDevice(ctx->device));
   Cfg& cfg = ctx->cfgs[cfg_id];
   if (!cfg.U64) CK(cudaMalloc(&cfg.U64, sizeof(double) * n));
-  if (!cfg.U32) CK(cudaMalloc(&cfg.U32, sizeof(float) * n));
+  if (!cfg.U32) CK(cudaMalloc(&cfg.U32, sizeof(float) * n32));
+  if (!cfg.U16) CK(cudaMalloc(&cfg.U16, sizeof(__half2) * n16));
+  CK(cudaMemcpy(cfg.U16, h16.data(), sizeof(__half2) * n16, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(cfg.U64, h64.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(cfg.U32, h32.data(), sizeof(float) * n, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(cfg.U32, h32.data(), sizeof(float) * n32, cudaMemcpyHostToDevice));
   cfg.has_gauge = true;
   cfg.anti = t_antiperiodic ? 1 : 0;
   return MDWF_OK;
@@ -971,6 +1402,29 @@ int mdwf_apply_mdwf_dev(mdwf_ctx* ctx, int cfg_id, const double* in, double* out
   if (!in || !out) return fail(ctx, MDWF_ERR_ARG, "apply_mdwf_dev: null pointer");
   CK(cudaSetDevice(ctx->device));
   return apply_dev(ctx, cfg, 1, dagger ? 1 : 0, 0, in, out, pick_stream(ctx, stream));
+}
+
+int mdwf_apply_schur_batch_dev(mdwf_ctx* ctx, int cfg_id, int n, const double* const* in, double* const* out,
+                               const double* masses, int dagger, int precision, int flags, void* stream) {
+  if (!ctx) return MDWF_ERR_ARG;
+  Cfg* cfg;
+  int rc = check_cfg(ctx, cfg_id, &cfg);
+  if (rc) return rc;
+  if (n < 1 || n > 1024 || !in || !out) return fail(ctx, MDWF_ERR_ARG, "apply_schur_batch_dev: bad n or pointers");
+  std::vector<double> m(n, cfg->act.mf);
+  for (int i = 0; i < n; i++) {
+    if (!in[i] || !out[i]) return fail(ctx, MDWF_ERR_ARG, "apply_schur_batch_dev: null field");
+    if (masses) m[i] = masses[i];
+  }
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = pick_stream(ctx, stream);
+  switch (precision) {
+    case MDWF_PREC_DOUBLE: return schur_batch_impl<double>(ctx, cfg, n, in, out, m, dagger, flags, st);
+    case MDWF_PREC_SINGLE: return schur_batch_impl<float>(ctx, cfg, n, in, out, m, dagger, flags, st);
+    case MDWF_PREC_HALF: return schur_batch_impl<__half>(ctx, cfg, n, in, out, m, dagger, flags, st);
+    case MDWF_PREC_BF16: return schur_batch_impl<__nv_bfloat16>(ctx, cfg, n, in, out, m, dagger, flags, st);
+    default: return fail(ctx, MDWF_ERR_ARG, "apply_schur_batch_dev: unknown precision");
+  }
 }
 
 int mdwf_extract_prop4d(const double* x5d, const int dims[4], int L5, double* q4d) {

@@ -7,7 +7,8 @@
 //   16-bit storage adds a scale per (h, s, r):   nrm[h][s][r] (float); the stored
 //                                                 values are v / nrm, nrm = max |v|.
 //   gauge field:                [parity][h][mu][18]   (3x3 complex, row major),
-//                                mu = 0..3 for x, y, z, t; U_mu(x) of the site x.
+//                                mu = 0..3 for x, y, z, t; U_mu(x) of the site x;
+//                                the FP32 copy pads each link to 20 floats.
 //   fifth-dimension matrices:   [r][chirality][L5][L5] real; chirality 0 acts on
 //                                spins 0,1 (P_+), chirality 1 on spins 2,3 (P_-).
 // Half-lattice index: lex = x + Lx (y + Ly (z + Lz t)), h = lex >> 1 (Lx even).
@@ -34,18 +35,20 @@ inline Geom make_geom(const int d[4]) {
   return g;
 }
 
+// 32-bit index arithmetic: lattices up to 2^31 sites.
 __host__ __device__ __forceinline__ void site_coords(const Geom& g, int par, long h, int c[4]) {
-  long r = h / g.Lxh;
-  int xh = (int)(h - r * g.Lxh);
-  c[1] = (int)(r % g.L[1]);
-  r /= g.L[1];
-  c[2] = (int)(r % g.L[2]);
-  c[3] = (int)(r / g.L[2]);
+  const int hi = (int)h;
+  int r = hi / g.Lxh;
+  const int xh = hi - r * g.Lxh;
+  int q = r / g.L[1];
+  c[1] = r - q * g.L[1];
+  c[3] = q / g.L[2];
+  c[2] = q - c[3] * g.L[2];
   c[0] = 2 * xh + ((c[1] + c[2] + c[3] + par) & 1);
 }
 
 __host__ __device__ __forceinline__ long lex_index(const Geom& g, const int c[4]) {
-  return c[0] + (long)g.L[0] * (c[1] + (long)g.L[1] * (c[2] + (long)g.L[2] * c[3]));
+  return (long)(c[0] + g.L[0] * (c[1] + g.L[1] * (c[2] + g.L[2] * c[3])));
 }
 
 // ---------------------------------------------------------------------------
@@ -120,7 +123,10 @@ __device__ __forceinline__ void store24<__half, float>(__half* __restrict__ v, f
   float m = 0.f;
 #pragma unroll
   for (int i = 0; i < 24; i++) m = fmaxf(m, fabsf(a[i]));
-  float inv = m > 0.f ? 1.0f / m : 0.f;
+  // A unit whose largest entry is below the smallest normal float is stored as
+  // zero (its reciprocal would overflow); such entries are < 1e-38 of O(1) data.
+  float inv = m >= 1.17549435e-38f ? 1.0f / m : 0.f;
+  if (inv == 0.f) m = 0.f;
   nrm[u] = m;
   uint4* p = reinterpret_cast<uint4*>(v + 24 * u);
 #pragma unroll
@@ -145,6 +151,88 @@ __device__ __forceinline__ void store24<__nv_bfloat16, float>(__nv_bfloat16* __r
   }
 }
 
+// Half of a stored spinor: part 0 = spins 0,1 (components 0..11), part 1 = spins 2,3.
+template <typename S, typename T>
+__device__ __forceinline__ void load_part(const S* __restrict__ v, const float* __restrict__ nrm, long u, int part,
+                                          T* o);
+template <>
+__device__ __forceinline__ void load_part<double, double>(const double* __restrict__ v, const float*, long u, int part,
+                                                          double* o) {
+  const double2* p = reinterpret_cast<const double2*>(v + 24 * u + 12 * part);
+#pragma unroll
+  for (int i = 0; i < 6; i++) { double2 t = __ldg(p + i); o[2 * i] = t.x; o[2 * i + 1] = t.y; }
+}
+template <>
+__device__ __forceinline__ void load_part<float, float>(const float* __restrict__ v, const float*, long u, int part,
+                                                        float* o) {
+  const float4* p = reinterpret_cast<const float4*>(v + 24 * u + 12 * part);
+#pragma unroll
+  for (int i = 0; i < 3; i++) { float4 t = __ldg(p + i); o[4*i] = t.x; o[4*i+1] = t.y; o[4*i+2] = t.z; o[4*i+3] = t.w; }
+}
+template <>
+__device__ __forceinline__ void load_part<__half, float>(const __half* __restrict__ v, const float* __restrict__ nrm,
+                                                         long u, int part, float* o) {
+  const uint2* p = reinterpret_cast<const uint2*>(v + 24 * u + 12 * part);
+  const float s = __ldg(nrm + u);
+#pragma unroll
+  for (int i = 0; i < 3; i++) {
+    uint2 t = __ldg(p + i);
+    const __half2* hh = reinterpret_cast<const __half2*>(&t);
+    float2 a = __half22float2(hh[0]), b = __half22float2(hh[1]);
+    o[4*i] = a.x * s; o[4*i+1] = a.y * s; o[4*i+2] = b.x * s; o[4*i+3] = b.y * s;
+  }
+}
+template <>
+__device__ __forceinline__ void load_part<__nv_bfloat16, float>(const __nv_bfloat16* __restrict__ v, const float*,
+                                                                long u, int part, float* o) {
+  const uint2* p = reinterpret_cast<const uint2*>(v + 24 * u + 12 * part);
+#pragma unroll
+  for (int i = 0; i < 3; i++) {
+    uint2 t = __ldg(p + i);
+    const __nv_bfloat162* hh = reinterpret_cast<const __nv_bfloat162*>(&t);
+    float2 a = __bfloat1622float2(hh[0]), b = __bfloat1622float2(hh[1]);
+    o[4*i] = a.x; o[4*i+1] = a.y; o[4*i+2] = b.x; o[4*i+3] = b.y;
+  }
+}
+
+// Plain (shared-memory) loads of a stored spinor, without the fp16 scale.
+template <typename S, typename T>
+__device__ __forceinline__ void load24_smem(const S* p, T a[24]);
+template <>
+__device__ __forceinline__ void load24_smem<double, double>(const double* p, double a[24]) {
+  const double2* q = reinterpret_cast<const double2*>(p);
+#pragma unroll
+  for (int i = 0; i < 12; i++) { double2 t = q[i]; a[2 * i] = t.x; a[2 * i + 1] = t.y; }
+}
+template <>
+__device__ __forceinline__ void load24_smem<float, float>(const float* p, float a[24]) {
+  const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+  for (int i = 0; i < 6; i++) { float4 t = q[i]; a[4*i] = t.x; a[4*i+1] = t.y; a[4*i+2] = t.z; a[4*i+3] = t.w; }
+}
+template <>
+__device__ __forceinline__ void load24_smem<__half, float>(const __half* p, float a[24]) {
+  const uint4* q = reinterpret_cast<const uint4*>(p);
+#pragma unroll
+  for (int i = 0; i < 3; i++) {
+    uint4 t = q[i];
+    const __half2* hh = reinterpret_cast<const __half2*>(&t);
+#pragma unroll
+    for (int j = 0; j < 4; j++) { float2 f = __half22float2(hh[j]); a[8*i+2*j] = f.x; a[8*i+2*j+1] = f.y; }
+  }
+}
+template <>
+__device__ __forceinline__ void load24_smem<__nv_bfloat16, float>(const __nv_bfloat16* p, float a[24]) {
+  const uint4* q = reinterpret_cast<const uint4*>(p);
+#pragma unroll
+  for (int i = 0; i < 3; i++) {
+    uint4 t = q[i];
+    const __nv_bfloat162* hh = reinterpret_cast<const __nv_bfloat162*>(&t);
+#pragma unroll
+    for (int j = 0; j < 4; j++) { float2 f = __bfloat1622float2(hh[j]); a[8*i+2*j] = f.x; a[8*i+2*j+1] = f.y; }
+  }
+}
+
 // Link loads (T precision, 18 reals).
 template <typename T>
 __device__ __forceinline__ void load_link(const T* __restrict__ U, long idx, T l[18]);
@@ -154,11 +242,17 @@ __device__ __forceinline__ void load_link<double>(const double* __restrict__ U, 
 #pragma unroll
   for (int i = 0; i < 9; i++) { double2 t = __ldg(p + i); l[2 * i] = t.x; l[2 * i + 1] = t.y; }
 }
+// FP32 links are padded to 20 floats (80 bytes) so that each is five aligned 16-byte loads.
+constexpr int kLinkStride32 = 20;
 template <>
 __device__ __forceinline__ void load_link<float>(const float* __restrict__ U, long idx, float l[18]) {
-  const float2* p = reinterpret_cast<const float2*>(U + 18 * idx);
-#pragma unroll
-  for (int i = 0; i < 9; i++) { float2 t = __ldg(p + i); l[2 * i] = t.x; l[2 * i + 1] = t.y; }
+  const float4* p = reinterpret_cast<const float4*>(U + kLinkStride32 * idx);
+  float4 t0 = __ldg(p), t1 = __ldg(p + 1), t2 = __ldg(p + 2), t3 = __ldg(p + 3), t4 = __ldg(p + 4);
+  l[0] = t0.x; l[1] = t0.y; l[2] = t0.z; l[3] = t0.w;
+  l[4] = t1.x; l[5] = t1.y; l[6] = t1.z; l[7] = t1.w;
+  l[8] = t2.x; l[9] = t2.y; l[10] = t2.z; l[11] = t2.w;
+  l[12] = t3.x; l[13] = t3.y; l[14] = t3.z; l[15] = t3.w;
+  l[16] = t4.x; l[17] = t4.y;
 }
 
 // ---------------------------------------------------------------------------
@@ -209,6 +303,57 @@ struct HopArgs {
   const int* active;    // [N] or null (all active)
   double* partials;     // [ntiles][N] |out|^2 per tile, or null
 };
+
+// Structured fifth-dimension epilogues of the fast hop kernel (hop_fast.cu).
+enum Epi { E_RAW = 0, E_BAINV = 1, E_AINVD_BD = 2, E_A_SAME = 3, E_AD_SAME_BD = 4, E_AINV_SAME = 5 };
+
+// A = alpha + beta P, B = b5 + c5 P; kap = beta / alpha; mass[r] = m_f of slot r.
+template <typename T>
+struct Fifth {
+  T alpha, beta, b5, c5, inv_alpha, kap;
+  T powL;          // (-kap)^L5
+  const T* mass;
+};
+
+template <typename S, typename T>
+struct FastArgs {
+  Geom g;
+  int L5, N;
+  int out_par, dagger, antiperiodic;
+  const S* in; const float* in_nrm;
+  const S* same; const float* same_nrm;
+  const S* add; const float* add_nrm;
+  S* out; float* out_nrm;
+  const T* U;
+  const __half2* U16;   // fp16 links [parity][h][mu][3][3] (tensor-core hop), or null
+  Fifth<T> f;
+  T g_same;             // coefficient of A same (E_A_SAME) / A^+ same (E_AD_SAME_BD)
+  T kappa;              // coefficient of the hop term
+  const int* active;
+  double* partials;
+};
+
+// Shared-memory staging of the neighbour sites (hop_staged_kernel).
+#define MDWF_TIMEOUT_CODE 1
+struct StageInfo {
+  unsigned spin_bytes;  // 8 * nsb * (L5 N) stored spinors
+  unsigned nrm_bytes;   // 8 * nsb * (L5 N) fp16 scales (0: loaded directly)
+  long long budget;     // bound of every barrier wait, in clock cycles
+  unsigned extra_tx;    // bytes a barrier waits for beyond the copies (0; nonzero only to test the timeout)
+  int* err;             // device status word: set to MDWF_TIMEOUT_CODE when a wait runs out
+};
+
+template <typename S, typename T>
+cudaError_t launch_fast(const FastArgs<S, T>& a, const Tiling& t, int epi, cudaStream_t st,
+                        const StageInfo* stage = nullptr);
+// Tensor-core hop (fp16 storage): usable when a block holds whole sites and L5 N % 8 == 0.
+bool mma_hop_usable(const Tiling& t, int L5, int N);
+cudaError_t launch_fast_mma(const FastArgs<__half, float>& a, const Tiling& t, int epi, cudaStream_t st);
+// Shared-memory bytes of a staged launch (0 if the tiling cannot be staged).
+template <typename S, typename T>
+size_t staged_smem_bytes(const Tiling& t, int L5, int N);
+template <typename S, typename T>
+int fast_max_threads();
 
 // Kernel launchers (hop.cu).
 template <typename S, typename T>

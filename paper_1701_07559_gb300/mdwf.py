@@ -43,16 +43,20 @@ _ERRNAMES = {v: k for k, v in globals().items() if k.startswith('MDWF_ERR_')}
 class mdwf_solver_opts(ctypes.Structure):
     _fields_ = [('precision', ctypes.c_int), ('max_iter', ctypes.c_int), ('delta', ctypes.c_double),
                 ('chunk', ctypes.c_int), ('use_graph', ctypes.c_int), ('nsb', ctypes.c_int),
-                ('reserved', ctypes.c_int * 6)]
+                ('profile', ctypes.c_int), ('wait_timeout_s', ctypes.c_double), ('timeout_test', ctypes.c_int),
+                ('hop_variant', ctypes.c_int), ('reserved', ctypes.c_int * 2)]
 
 
 class mdwf_solve_stats(ctypes.Structure):
     _fields_ = [('iters', ctypes.c_int), ('reliable_updates', ctypes.c_int), ('converged', ctypes.c_int),
-                ('reserved0', ctypes.c_int), ('rel_true_resid', ctypes.c_double), ('time_s', ctypes.c_double)]
+                ('hop_launches', ctypes.c_int), ('rel_true_resid', ctypes.c_double), ('time_s', ctypes.c_double),
+                ('hop_ms', ctypes.c_double), ('kernel_launches', ctypes.c_longlong),
+                ('hop_units', ctypes.c_longlong)]
 
     def as_dict(self):
         return {'iters': self.iters, 'reliable_updates': self.reliable_updates, 'converged': bool(self.converged),
-                'rel_true_resid': self.rel_true_resid, 'time_s': self.time_s}
+                'rel_true_resid': self.rel_true_resid, 'time_s': self.time_s, 'hop_launches': self.hop_launches,
+                'hop_ms': self.hop_ms, 'kernel_launches': self.kernel_launches, 'hop_units': self.hop_units}
 
 
 class MdwfError(RuntimeError):
@@ -81,6 +85,7 @@ _sig = {
                               ctypes.POINTER(mdwf_solver_opts), ctypes.POINTER(mdwf_solve_stats)]),
     'mdwf_solve_batch_dev': (_I, [_P, _I, _I, ctypes.POINTER(_P), _P, ctypes.POINTER(_P), _D,
                                   ctypes.POINTER(mdwf_solver_opts), ctypes.POINTER(mdwf_solve_stats), _P]),
+    'mdwf_apply_schur_batch_dev': (_I, [_P, _I, _I, ctypes.POINTER(_P), ctypes.POINTER(_P), _P, _I, _I, _I, _P]),
     'mdwf_apply_dslash_dev': (_I, [_P, _I, _P, _P, _I, _I, _P]),
     'mdwf_apply_mdwf_dev': (_I, [_P, _I, _P, _P, _I, _P]),
     'mdwf_extract_prop4d': (_I, [_P, ctypes.POINTER(_I), _I, _P]),
@@ -228,12 +233,21 @@ def mdwf_solve(ctx, cfg_id, src, tol, opts=None):
     return x, st.as_dict()
 
 
-def mdwf_solve_batch(ctx, cfg_id, srcs, tol, masses=None, opts=None, raise_on_nonconv=True):
-    """Solve len(srcs) systems in one batch.  Returns (list of x, list of stats dicts)."""
+def mdwf_solve_batch(ctx, cfg_id, srcs, tol, masses=None, opts=None, raise_on_nonconv=True, out=None):
+    """Solve len(srcs) systems in one batch.  Returns (list of x, list of stats dicts).
+
+    ``out``: optional list of preallocated contiguous complex128 host arrays (for
+    example views of pinned memory) that receive the solutions."""
     shape = _shape5(ctx, cfg_id)
     n = len(srcs)
     hs = [_host(s, shape) for s in srcs]
-    xs = [np.empty(shape, dtype=np.complex128) for _ in range(n)]
+    if out is not None:
+        xs = list(out)
+        for x in xs:
+            if x.dtype != np.complex128 or x.shape != shape or not x.flags['C_CONTIGUOUS']:
+                raise ValueError('out arrays must be contiguous complex128 of shape %s' % (shape,))
+    else:
+        xs = [np.empty(shape, dtype=np.complex128) for _ in range(n)]
     sp = (_P * n)(*[s.ctypes.data for s in hs])
     xp = (_P * n)(*[x.ctypes.data for x in xs])
     m = None
@@ -283,6 +297,26 @@ def mdwf_solve_batch_dev(ctx, cfg_id, srcs, xs, tol, masses=None, opts=None, str
     if rc != MDWF_OK and (raise_on_nonconv or rc != MDWF_ERR_NOT_CONVERGED):
         _check(ctx, rc)
     return [s.as_dict() for s in st]
+
+
+HOP_AUTO, HOP_DIRECT, HOP_STAGED = 0, 1, 2
+
+
+def mdwf_apply_schur_batch_dev(ctx, cfg_id, ins, outs, masses=None, dagger=0, precision=MDWF_PREC_HALF,
+                               hop_variant=HOP_AUTO, stream=None):
+    """Batched Schur operator (the solver's hot kernels) on torch CUDA tensors."""
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    shape = _shape5(ctx, cfg_id)
+    n = len(ins)
+    ip = (_P * n)(*[_dev_ptr(t, shape) for t in ins])
+    op = (_P * n)(*[_dev_ptr(t, shape) for t in outs])
+    m = None
+    if masses is not None:
+        m = np.ascontiguousarray(masses, dtype=np.float64)
+    sh = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+    _check(ctx, _lib.mdwf_apply_schur_batch_dev(ctx.handle, int(cfg_id), n, ip, op, _ptr(m) if m is not None else None,
+                                                int(dagger), int(precision), int(hop_variant), sh))
 
 
 def mdwf_apply_dslash_dev(ctx, cfg_id, psi, out, out_parity=-1, dagger=0, stream=None):

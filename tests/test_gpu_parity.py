@@ -230,3 +230,51 @@ def test_solve_errors():
         assert e.value.code == M.MDWF_ERR_STATE
     finally:
         M.mdwf_destroy(ctx)
+
+
+def test_bounded_wait_reports_timeout_and_context_survives():
+    """A staged-copy wait that runs out (the test knob makes each barrier expect bytes
+    that never arrive) ends the solve with MDWF_ERR_TIMEOUT; the same context then
+    solves normally."""
+    L = Lat(*CASES[0])
+    try:
+        b = synth.gaussian_spinor(L.shape, 17)
+        bad = M.mdwf_default_opts(precision='half', timeout_test=1, wait_timeout_s=0.05)
+        with pytest.raises(M.MdwfError) as e:
+            M.mdwf_solve(L.ctx, 0, b, 1e-10, bad)
+        assert e.value.code == M.MDWF_ERR_TIMEOUT
+        x, st = M.mdwf_solve(L.ctx, 0, b, 1e-10, M.mdwf_default_opts(precision='half'))
+        _check_solution(L, b, x, st)
+    finally:
+        L.close()
+
+
+@pytest.mark.parametrize('precision,tol', [('double', 1e-13), ('single', 2e-6), ('half', 4e-3), ('bf16', 3e-2)])
+@pytest.mark.parametrize('dagger', [0, 1])
+@pytest.mark.parametrize('variant', [0, 1, 2])
+@pytest.mark.parametrize('L5,masses', [(5, [0.05, 0.01, 0.2, 0.0022, 0.1]),            # L5 N = 25
+                                       (4, [0.05, 0.01, 0.2, 0.0022, 0.1, 0.3])])      # L5 N = 24: tensor-core tiles
+def test_schur_batch_multi_rhs(precision, tol, dagger, variant, L5, masses):
+    """The batched Schur operator (the solver's kernels, N RHS with different masses,
+    every hop variant) against the oracle, slot by slot."""
+    import torch
+    dims = (6, 4, 4, 6)
+    act = (1.2, 1.25, 0.25, 0.05)
+    U = synth.random_gauge(dims, 19, 0.5)
+    ctx = M.mdwf_create(dims, 0)
+    try:
+        M.mdwf_load_gauge(ctx, 0, U, 1)
+        M.mdwf_set_action(ctx, 0, *act, L5)
+        shape = (L5,) + tuple(reversed(dims)) + (4, 3)
+        ev = O.parity_mask(dims)
+        xs = [O.restrict(synth.gaussian_spinor(shape, 200 + i), ev) for i in range(len(masses))]
+        ins = [torch.from_numpy(x).cuda() for x in xs]
+        outs = [torch.empty_like(t) for t in ins]
+        M.mdwf_apply_schur_batch_dev(ctx, 0, ins, outs, masses=masses, dagger=dagger, precision=precision,
+                                     hop_variant=variant)
+        f = O.schur_op_dag if dagger else O.schur_op
+        for x, o, m in zip(xs, outs, masses):
+            ref = f(U, x, act[0], act[1], act[2], m)
+            assert _rel(o.cpu().numpy(), ref) < tol
+    finally:
+        M.mdwf_destroy(ctx)
