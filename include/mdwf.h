@@ -176,6 +176,38 @@ int mdwf_solve_batch_dev(mdwf_ctx* ctx, int cfg_id, int n, const double* const* 
 int mdwf_apply_schur_batch_dev(mdwf_ctx* ctx, int cfg_id, int n, const double* const* in, double* const* out,
                                const double* masses, int dagger, int precision, int hop_variant, void* stream);
 
+/* mdwf_apply_schur_batch_dev for callers that cannot allocate device memory.
+ *
+ * Some callers may not call cudaMalloc at all: a host application whose own
+ * pool already owns the device memory, or a latency-bound path that cannot
+ * accept the device-wide synchronisation an allocation can cause.  This entry
+ * point computes the same result as mdwf_apply_schur_batch_dev (same kernels,
+ * hop variant 1) but allocates nothing.  Its scratch -- packed copies of the
+ * inputs, two intermediate fields, the packed output and the per-RHS masses --
+ * lives in one fixed device array of MDWF_NOALLOC_SCRATCH_BYTES bytes that is
+ * part of the library's device image: every GPU on which the library's device
+ * code is loaded holds those bytes until the process exits.  The caller still
+ * allocates and passes the input and output fields.
+ *
+ * Limit: 4 fields of (V/2) * L5 * n stored spinors (192, 96, 48 or 48 bytes each
+ * for double, single, half, bf16, plus a 4-byte scale each for half) plus the
+ * masses must fit, e.g. FP64 up to about 87,000 (site, slice, RHS) units.  A
+ * larger problem is rejected with MDWF_ERR_ARG and a message giving the size.
+ *
+ * The first call on a device looks up the array's device address (with that
+ * device current) and caches it; make that first call before any stream
+ * capture.  Every call uses the same array, which keeps the previous call's
+ * contents (the kernels overwrite what they read, and the one field that must
+ * start at zero is cleared by the call itself); calls that overlap on the GPU --
+ * from several streams or host threads at once -- race on the array and must be
+ * serialised by the caller.  Returns when the work on `stream` has finished.
+ * The paper has no counterpart to this entry point.
+ * Errors: ARG (including a problem too large for the array), STATE, CUDA. */
+#define MDWF_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
+int mdwf_apply_schur_batch_dev_noalloc(mdwf_ctx* ctx, int cfg_id, int n, const double* const* in,
+                                       double* const* out, const double* masses, int dagger, int precision,
+                                       void* stream);
+
 /* Device-pointer variants of the operator applies, on `stream` (asynchronous). */
 int mdwf_apply_dslash_dev(mdwf_ctx* ctx, int cfg_id, const double* in, double* out, int out_parity, int dagger,
                           void* stream);

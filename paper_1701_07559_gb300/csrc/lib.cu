@@ -1440,3 +1440,122 @@ int mdwf_extract_prop4d(const double* x5d, const int dims[4], int L5, double* q4
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// The batched Schur operator without device allocation
+// ===========================================================================
+// For callers that may not call cudaMalloc (the device memory belongs to another
+// pool, or an allocation's implicit device synchronisation is not acceptable on
+// their path).  All scratch comes from one fixed array that is part of this
+// library's device image; see mdwf_apply_schur_batch_dev_noalloc in mdwf.h.
+#include <mutex>
+
+namespace {
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[MDWF_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+unsigned char* g_noalloc_addr[kMaxDevices] = {nullptr};   // device address of the array, per device
+
+// Device address of the scratch array on ctx's device (which must be current).
+// In host code the array's name is only a stand-in, so the address is looked up
+// once per device and cached.
+int noalloc_scratch(mdwf_ctx* ctx, unsigned char** out) {
+  if (ctx->device < 0 || ctx->device >= kMaxDevices) return fail(ctx, MDWF_ERR_ARG, "device index out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (g_noalloc_addr[ctx->device] == nullptr) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || p == nullptr)
+      return fail(ctx, MDWF_ERR_CUDA, std::string("cudaGetSymbolAddress of the scratch array: ") +
+                                          cudaGetErrorString(e));
+    g_noalloc_addr[ctx->device] = static_cast<unsigned char*>(p);
+  }
+  *out = g_noalloc_addr[ctx->device];
+  return MDWF_OK;
+}
+
+inline size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+template <typename S>
+int schur_batch_noalloc_impl(mdwf_ctx* ctx, Cfg* cfg, int n, const double* const* in, double* const* out,
+                             const std::vector<double>& masses, int dagger, cudaStream_t st) {
+  using T = typename StoreTraits<S>::T;
+  const Geom& g = ctx->g;
+  const int L5 = cfg->act.L5, N = n;
+  const size_t units = (size_t)g.Vh * L5 * N;
+  const size_t fbytes = round256(sizeof(S) * 24 * units);
+  const size_t nbytes = StoreTraits<S>::kNorm ? round256(sizeof(float) * units) : 0;
+  const size_t mbytes = round256(sizeof(T) * N);
+  const size_t need = mbytes + 4 * (fbytes + nbytes);
+  if (need > (size_t)MDWF_NOALLOC_SCRATCH_BYTES)
+    return fail(ctx, MDWF_ERR_ARG, "apply_schur_batch_dev_noalloc: this problem needs " + std::to_string(need) +
+                                       " bytes of scratch, more than the fixed " +
+                                       std::to_string((size_t)MDWF_NOALLOC_SCRATCH_BYTES) + " bytes");
+  unsigned char* base = nullptr;
+  int rc = noalloc_scratch(ctx, &base);
+  if (rc) return rc;
+  // carve: [masses][in][u][t][out], each field followed by its fp16 scales
+  T* mass = reinterpret_cast<T*>(base);
+  F<S> f[4];
+  unsigned char* p = base + mbytes;
+  for (int i = 0; i < 4; i++) {
+    f[i].v = reinterpret_cast<S*>(p);
+    p += fbytes;
+    f[i].n = nbytes ? reinterpret_cast<float*>(p) : nullptr;
+    p += nbytes;
+  }
+  F<S> fin = f[0], fu = f[1], ft = f[2], fo = f[3];
+  std::vector<T> mh(masses.begin(), masses.end());
+  CK(cudaMemcpyAsync(mass, mh.data(), sizeof(T) * N, cudaMemcpyHostToDevice, st));
+  FastOp<S, T> op;
+  op.g = g; op.L5 = L5; op.N = N; op.anti = cfg->anti; op.st = st;
+  op.U = std::is_same<T, double>::value ? (const T*)cfg->U64 : (const T*)cfg->U32;
+  op.f = make_fifth<T>(cfg->act, mass);
+  choose_hop(op, cfg, 0, HOP_DIRECT, nullptr);
+  Tiling tb = make_tiling(g.Vh, L5, N, 2, 1024);
+  for (int i = 0; i < N; i++) CK(pack_rhs<S>(in[i], fin.v, fin.n, g, L5, N, 0, i, st));
+  if (!dagger) {
+    CK(bop<S>(fin.v, fin.n, fu.v, fu.n, op.f, tb, g.Vh, L5, N, nullptr, st));
+    CK(op.mhat(fin, fu, ft, fo, nullptr, nullptr));
+  } else {
+    CK(op.mhat_dag(fin, ft, fo, nullptr, nullptr));
+  }
+  // the intermediate odd field is no longer needed: zero it and use it as the
+  // source of the odd sites of every output (they must come out zero)
+  CK(cudaMemsetAsync(ft.v, 0, fbytes, st));
+  if (nbytes) CK(cudaMemsetAsync(ft.n, 0, nbytes, st));
+  for (int i = 0; i < N; i++) {
+    CK(unpack_rhs<S>(fo.v, fo.n, out[i], g, L5, N, 0, i, st));
+    CK(unpack_rhs<S>(ft.v, ft.n, out[i], g, L5, N, 1, i, st));
+  }
+  CK(cudaStreamSynchronize(st));
+  return MDWF_OK;
+}
+
+}  // namespace
+
+extern "C" int mdwf_apply_schur_batch_dev_noalloc(mdwf_ctx* ctx, int cfg_id, int n, const double* const* in,
+                                                  double* const* out, const double* masses, int dagger,
+                                                  int precision, void* stream) {
+  if (!ctx) return MDWF_ERR_ARG;
+  Cfg* cfg;
+  int rc = check_cfg(ctx, cfg_id, &cfg);
+  if (rc) return rc;
+  if (n < 1 || n > 1024 || !in || !out) return fail(ctx, MDWF_ERR_ARG, "apply_schur_batch_dev_noalloc: bad n or pointers");
+  std::vector<double> m(n, cfg->act.mf);
+  for (int i = 0; i < n; i++) {
+    if (!in[i] || !out[i]) return fail(ctx, MDWF_ERR_ARG, "apply_schur_batch_dev_noalloc: null field");
+    if (masses) m[i] = masses[i];
+  }
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = pick_stream(ctx, stream);
+  switch (precision) {
+    case MDWF_PREC_DOUBLE: return schur_batch_noalloc_impl<double>(ctx, cfg, n, in, out, m, dagger, st);
+    case MDWF_PREC_SINGLE: return schur_batch_noalloc_impl<float>(ctx, cfg, n, in, out, m, dagger, st);
+    case MDWF_PREC_HALF: return schur_batch_noalloc_impl<__half>(ctx, cfg, n, in, out, m, dagger, st);
+    case MDWF_PREC_BF16: return schur_batch_noalloc_impl<__nv_bfloat16>(ctx, cfg, n, in, out, m, dagger, st);
+    default: return fail(ctx, MDWF_ERR_ARG, "apply_schur_batch_dev_noalloc: unknown precision");
+  }
+}

@@ -86,6 +86,7 @@ _sig = {
     'mdwf_solve_batch_dev': (_I, [_P, _I, _I, ctypes.POINTER(_P), _P, ctypes.POINTER(_P), _D,
                                   ctypes.POINTER(mdwf_solver_opts), ctypes.POINTER(mdwf_solve_stats), _P]),
     'mdwf_apply_schur_batch_dev': (_I, [_P, _I, _I, ctypes.POINTER(_P), ctypes.POINTER(_P), _P, _I, _I, _I, _P]),
+    'mdwf_apply_schur_batch_dev_noalloc': (_I, [_P, _I, _I, ctypes.POINTER(_P), ctypes.POINTER(_P), _P, _I, _I, _P]),
     'mdwf_apply_dslash_dev': (_I, [_P, _I, _P, _P, _I, _I, _P]),
     'mdwf_apply_mdwf_dev': (_I, [_P, _I, _P, _P, _I, _P]),
     'mdwf_extract_prop4d': (_I, [_P, ctypes.POINTER(_I), _I, _P]),
@@ -317,6 +318,29 @@ def mdwf_apply_schur_batch_dev(ctx, cfg_id, ins, outs, masses=None, dagger=0, pr
     sh = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
     _check(ctx, _lib.mdwf_apply_schur_batch_dev(ctx.handle, int(cfg_id), n, ip, op, _ptr(m) if m is not None else None,
                                                 int(dagger), int(precision), int(hop_variant), sh))
+
+
+MDWF_NOALLOC_SCRATCH_BYTES = 64 * 1024 * 1024
+
+
+def mdwf_apply_schur_batch_dev_noalloc(ctx, cfg_id, ins, outs, masses=None, dagger=0, precision=MDWF_PREC_HALF,
+                                       stream=None):
+    """The batched Schur operator without any device allocation (scratch in a fixed
+    library array of MDWF_NOALLOC_SCRATCH_BYTES; see include/mdwf.h for the limit and
+    the rule that overlapping calls race)."""
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    shape = _shape5(ctx, cfg_id)
+    n = len(ins)
+    ip = (_P * n)(*[_dev_ptr(t, shape) for t in ins])
+    op = (_P * n)(*[_dev_ptr(t, shape) for t in outs])
+    m = None
+    if masses is not None:
+        m = np.ascontiguousarray(masses, dtype=np.float64)
+    sh = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+    _check(ctx, _lib.mdwf_apply_schur_batch_dev_noalloc(ctx.handle, int(cfg_id), n, ip, op,
+                                                        _ptr(m) if m is not None else None, int(dagger),
+                                                        int(precision), sh))
 
 
 def mdwf_apply_dslash_dev(ctx, cfg_id, psi, out, out_parity=-1, dagger=0, stream=None):
