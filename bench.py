@@ -45,7 +45,8 @@ def parse():
                     help="'op': only apply the batched Schur operator (the solver's hop kernels), for profiling")
     ap.add_argument('--lattice', default=None, help="op mode: Lx,Ly,Lz,Lt instead of the workload's 16,16,16,48")
     ap.add_argument('--hop-variant', type=int, default=0,
-                    help='0 automatic (tensor-core hop for fp16), 1 CUDA-core direct loads, 2 CUDA-core staged')
+                    help='0 automatic, 1 CUDA-core direct loads, 2 CUDA-core staged, 3 tensor-core (fp16)')
+    ap.add_argument('--nsb', type=int, default=0, help='sites per thread block (0: chosen by the library)')
     return ap.parse_args()
 
 
@@ -233,7 +234,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     dsrc = [torch.from_numpy(s).to('cuda') for s in srcs]
     dx = [torch.empty_like(s) for s in dsrc]
-    opts = M.mdwf_default_opts(precision=prec, profile=1, hop_variant=args.hop_variant)
+    opts = M.mdwf_default_opts(precision=prec, profile=1, hop_variant=args.hop_variant, nsb=args.nsb)
 
     def barrier():
         if dist is not None:
@@ -289,7 +290,7 @@ def run_ours(args):
     # end to end through the host-pointer C ABI call, pinned host buffers
     pin_src = [torch.from_numpy(s).pin_memory().numpy() for s in srcs]
     pin_x = [torch.empty(s.shape, dtype=torch.complex128).pin_memory().numpy() for s in srcs]
-    opts_e2e = M.mdwf_default_opts(precision=prec, hop_variant=args.hop_variant)
+    opts_e2e = M.mdwf_default_opts(precision=prec, hop_variant=args.hop_variant, nsb=args.nsb)
     M.mdwf_solve_batch(ctx, 0, pin_src, W['tol'], opts=opts_e2e, out=pin_x)
     torch.cuda.synchronize()
     barrier()
@@ -386,7 +387,7 @@ def run_op(args):
     M.mdwf_set_action(ctx, 0, W['M5'], W['b5'], W['c5'], W['mf'], W['L5'])
     Lx, Ly, Lz, Lt = W['dims']
     shape = (W['L5'], Lt, Lz, Ly, Lx, 4, 3)
-    variant = args.hop_variant
+    variant = args.hop_variant | (args.nsb << 8)
     ins = [torch.from_numpy(synth.gaussian_spinor(shape, 50 + i)).to('cuda') for i in range(args.rhs)]
     outs = [torch.empty_like(x) for x in ins]
     t = []
@@ -400,7 +401,7 @@ def run_op(args):
             t.append(time.perf_counter() - t0)
     M.mdwf_destroy(ctx)
     print(json.dumps({'mode': 'op', 'rhs': args.rhs, 'precision': args.precision, 'lattice': W['dims'],
-                      'hop_variant': args.hop_variant,
+                      'hop_variant': args.hop_variant, 'nsb': args.nsb,
                       'ms_per_pair_of_applies': 1e3 * statistics.mean(t) if t else None}), flush=True)
     return 0
 

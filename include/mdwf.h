@@ -71,9 +71,10 @@ typedef struct {
                             the call with MDWF_ERR_TIMEOUT and leaves the context usable */
   int timeout_test;      /* testing only: 1 makes each staged-copy wait expect bytes that never
                             arrive, so the bound above must end the call with MDWF_ERR_TIMEOUT */
-  int hop_variant;       /* 0: automatic (tensor-core hop for fp16 storage when a block holds whole
-                            sites, else CUDA-core); 1: CUDA-core hop with direct neighbour loads;
-                            2: CUDA-core hop with neighbours staged in shared memory by bulk copies */
+  int hop_variant;       /* 0: automatic (today the CUDA-core hop with direct loads, the fastest
+                            measured); 1: CUDA-core hop with direct neighbour loads; 2: CUDA-core hop
+                            with neighbours staged in shared memory by bulk copies; 3: tensor-core
+                            colour multiply (fp16 storage, L5 N a multiple of 16), else as 0 */
   int reserved[2];
 } mdwf_solver_opts;
 
@@ -170,8 +171,9 @@ int mdwf_solve_batch_dev(mdwf_ctx* ctx, int cfg_id, int n, const double* const* 
  * with m_i = masses[i] (host array; NULL = the action's m_f).  It runs the same
  * kernels, tiling and storage precision (MDWF_PREC_*) as the CG iterations of
  * mdwf_solve_batch; odd sites of in_i are ignored and odd sites of out_i set
- * to zero.  hop_variant as in mdwf_solver_opts.  Returns after the work on
- * `stream` has finished.
+ * to zero.  hop_variant as in mdwf_solver_opts in its low 8 bits; bits 8..15, if
+ * nonzero, fix the number of sites per thread block (a tuning knob).  Returns
+ * after the work on `stream` has finished.
  * Errors: ARG, STATE, NOMEM, CUDA, TIMEOUT. */
 int mdwf_apply_schur_batch_dev(mdwf_ctx* ctx, int cfg_id, int n, const double* const* in, double* const* out,
                                const double* masses, int dagger, int precision, int hop_variant, void* stream);

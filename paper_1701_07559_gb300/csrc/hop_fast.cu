@@ -81,12 +81,12 @@ __device__ __forceinline__ void project(const T* p, T sg, T* h) {
 // fp16: project the packed (scaled) values with half2 arithmetic, then unpack and scale.
 template <int MU>
 __device__ __forceinline__ void project_half(const uint4 q[3], float s, float sg, float* h) {
-  const __half2* w = reinterpret_cast<const __half2*>(q);   // w[3 * spin + colour]
+  const __half2* w = reinterpret_cast<const __half2*>(q);   // w[4 * colour + spin] (colour-major storage)
   const __half2 pp = __floats2half2_rn(sg, sg);
   const __half2 mp = __floats2half2_rn(-sg, sg);             // times swapped z: sg * i * z
 #pragma unroll
   for (int c = 0; c < 3; c++) {
-    const __half2 p0 = w[c], p1 = w[3 + c], p2 = w[6 + c], p3 = w[9 + c];
+    const __half2 p0 = w[4 * c], p1 = w[4 * c + 1], p2 = w[4 * c + 2], p3 = w[4 * c + 3];
     __half2 h0, h1;
     if (MU == 0) {
       h0 = __hfma2(__lowhigh2highlow(p3), mp, p0);
@@ -639,92 +639,87 @@ int max_threads_one() {
 }
 
 // ---------------------------------------------------------------------------
-// Tensor-core variant for fp16 storage.  For one direction, the colour
-// multiply of all (slice, RHS) rows of a site by the same link is a small dense
-// product: rows = (unit, projected spin k), columns = colour (re, im).  A warp
-// takes 8 units per mma.sync.m16n8k8 (fp16 operands, FP32 accumulation):
-//   A (16 x 8): row g = unit g, k = 0; row g + 8 = unit g, k = 1; columns 2b, 2b+1 =
-//               (re, im) of colour b of the projected half spinor h (b < 3);
-//   B (8 x 8):  the real form of the link, B[2b][2a] = Re U_ab, B[2b+1][2a] = -Im U_ab,
-//               B[2b][2a+1] = Im U_ab, B[2b+1][2a+1] = Re U_ab (U^+ for backward hops);
-//   D (16 x 8): (re, im) of colour a of chi = U h, in FP32.
-// Lane (g, c) with c = lane % 4 < 3 loads the four spins of colour c of unit g,
-// projects them in half2 arithmetic, and accumulates scale * chi and the
-// spin-rotated scale * chi into FP32 registers (scales differ between units,
-// so they are applied after the product).  Lanes with c = 3 carry zeros.
+// Tensor-core variant for fp16 storage.  For one direction mu, the colour
+// multiply of all (slice, RHS) units of a site by the same link is a small
+// dense product.  A warp takes a tile of 16 units of one site and, per mu,
+// four mma.sync.m16n8k16 (fp16 operands, FP32 accumulation):
+//   A (16 x 16): row i = unit i of the tile; columns 0..7 = (re, im) of the
+//                three colours (+ padding) of the forward term's projected
+//                spin component, columns 8..15 the backward term's;
+//   B (16 x 8):  rows 0..7 the real form of U_mu(x) (forward), rows 8..15 of
+//                U_mu(x - mu)^+ (backward): B[2b][2a] = Re W_ab, B[2b+1][2a] = -Im W_ab,
+//                B[2b][2a+1] = Im W_ab, B[2b+1][2a+1] = Re W_ab;
+//   C (16 x 8):  (re, im) of colour a of sum_d W_d h_d, accumulated over mu.
+// The two spin components k of the projected spinor h and of the rotated
+// spinor g = sg e_mu^+ h (which feeds the lower spins) use one mma each:
+// up_k += h_k B, lo_k += g_k B.  Every unit has its own fp16 scale per
+// neighbour; they are divided by the unit's largest neighbour scale and folded
+// into A (so A stays within fp16 range), and the FP32 result is multiplied by
+// that largest scale at the end.  Lane (g, c), c = lane % 4, loads colour c of
+// units g and g + 8 (one 16-byte word each); lanes with c = 3 carry zeros.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void mma_16816_like(uint32_t a0, uint32_t a1, uint32_t b0, float d[4]) {
-  asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%7,%8,%9,%10};"
-               : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
-               : "r"(a0), "r"(a1), "r"(b0), "f"(0.f), "f"(0.f), "f"(0.f), "f"(0.f));
+__device__ __forceinline__ void mma_m16n8k16(const uint32_t a[4], uint32_t b0, uint32_t b1, float d[4]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
 __device__ __forceinline__ uint32_t h2u(__half2 h) { return *reinterpret_cast<uint32_t*>(&h); }
+__device__ __forceinline__ __half2 u2h(uint32_t u) { return *reinterpret_cast<__half2*>(&u); }
+__device__ __forceinline__ uint32_t swap_hl(uint32_t x) { return __byte_perm(x, 0, 0x1032); }
+constexpr uint32_t kNegHi = 0x80000000u, kNegLo = 0x00008000u;
 
-template <int MU, bool FWD>
-__device__ __forceinline__ void mma_term(const FastArgs<__half, float>& a, const Site& x, long h, int lu, int upb,
-                                         int g, int c, float* up, float* lo) {
-  const int hn = nbr_half<MU, FWD>(a.g, x);
-  const float sg = (a.dagger ? 1.f : -1.f) * (FWD ? 1.f : -1.f);
-  // A fragment: projected spinor, colour c of unit g (zero in the padding lanes)
-  uint32_t a0 = 0u, a1 = 0u;
-  const long u = (long)hn * upb + lu;
-  float s = __ldg(a.in_nrm + u);
-  if (c < 3) {
-    const uint32_t* w = reinterpret_cast<const uint32_t*>(a.in) + 12 * u + c;
-    uint32_t q0 = __ldg(w), q1 = __ldg(w + 3), q2 = __ldg(w + 6), q3 = __ldg(w + 9);
-    const __half2 p0 = *reinterpret_cast<__half2*>(&q0), p1 = *reinterpret_cast<__half2*>(&q1);
-    const __half2 p2 = *reinterpret_cast<__half2*>(&q2), p3 = *reinterpret_cast<__half2*>(&q3);
-    const __half2 pp = __floats2half2_rn(sg, sg);
-    const __half2 mp = __floats2half2_rn(-sg, sg);
-    __half2 h0, h1;
-    if (MU == 0) {
-      h0 = __hfma2(__lowhigh2highlow(p3), mp, p0);
-      h1 = __hfma2(__lowhigh2highlow(p2), mp, p1);
-    } else if (MU == 1) {
-      h0 = __hfma2(p3, __hneg2(pp), p0);
-      h1 = __hfma2(p2, pp, p1);
-    } else if (MU == 2) {
-      h0 = __hfma2(__lowhigh2highlow(p2), mp, p0);
-      h1 = __hfma2(__lowhigh2highlow(p3), __hneg2(mp), p1);
-    } else {
-      h0 = __hfma2(p2, pp, p0);
-      h1 = __hfma2(p3, pp, p1);
-    }
-    a0 = h2u(h0);
-    a1 = h2u(h1);
+// Projected (h0, h1) and rotated (g0, g1) half spinors of colour c of one unit,
+// scaled by r (fp16 pair), from the 16-byte word q = spins 0..3 of that colour.
+template <int MU>
+__device__ __forceinline__ void mma_project(uint4 q, __half2 r, bool neg_sg, uint32_t& h0, uint32_t& h1, uint32_t& g0,
+                                            uint32_t& g1) {
+  const uint32_t sgn = neg_sg ? (kNegHi | kNegLo) : 0u;   // multiply by sg = -1
+  const __half2 p0 = u2h(q.x), p1 = u2h(q.y), p2 = u2h(q.z), p3 = u2h(q.w);
+  __half2 a0, a1;
+  // h = psi_up + sg e_mu psi_lo ; e_x = i sigma_x, e_y = -i sigma_y, e_z = i sigma_z, e_t = 1
+  if (MU == 0) {        // (i p3, i p2)
+    a0 = __hadd2(p0, u2h(swap_hl(h2u(p3)) ^ kNegLo ^ sgn));
+    a1 = __hadd2(p1, u2h(swap_hl(h2u(p2)) ^ kNegLo ^ sgn));
+  } else if (MU == 1) { // (-p3, p2)
+    a0 = __hadd2(p0, u2h(h2u(p3) ^ (kNegHi | kNegLo) ^ sgn));
+    a1 = __hadd2(p1, u2h(h2u(p2) ^ sgn));
+  } else if (MU == 2) { // (i p2, -i p3)
+    a0 = __hadd2(p0, u2h(swap_hl(h2u(p2)) ^ kNegLo ^ sgn));
+    a1 = __hadd2(p1, u2h(swap_hl(h2u(p3)) ^ kNegHi ^ sgn));
+  } else {              // (p2, p3)
+    a0 = __hadd2(p0, u2h(h2u(p2) ^ sgn));
+    a1 = __hadd2(p1, u2h(h2u(p3) ^ sgn));
   }
-  if (MU == 3 && a.antiperiodic && (FWD ? x.c[3] == a.g.L[3] - 1 : x.c[3] == 0)) s = -s;
-  // B fragment: rows 2c, 2c+1 (colour b = c of h), column g (colour a = g / 2, part q = g % 2)
-  uint32_t b0 = 0u;
-  const int ca = g >> 1, q = g & 1;
-  if (c < 3 && ca < 3) {
-    const long link = FWD ? ((long)a.out_par * a.g.Vh + h) * 4 + MU : ((long)(1 - a.out_par) * a.g.Vh + hn) * 4 + MU;
-    // U_ab (forward) or (U^+)_ab = conj(U_ba) (backward), a = ca, b = c
-    const __half2 e = a.U16[link * 9 + (FWD ? ca * 3 + c : c * 3 + ca)];
-    const float2 f = __half22float2(e);
-    const float ur = f.x, ui = FWD ? f.y : -f.y;
-    b0 = h2u(q == 0 ? __floats2half2_rn(ur, -ui) : __floats2half2_rn(ui, ur));
+  h0 = h2u(__hmul2(a0, r));
+  h1 = h2u(__hmul2(a1, r));
+  // g = sg e_mu^+ h ;  -i z = swap(z) with the high half negated, i z = swap(z) with the low half negated
+  if (MU == 0) {        // (-i h1, -i h0)
+    g0 = swap_hl(h1) ^ kNegHi ^ sgn;
+    g1 = swap_hl(h0) ^ kNegHi ^ sgn;
+  } else if (MU == 1) { // (h1, -h0)
+    g0 = h1 ^ sgn;
+    g1 = h0 ^ (kNegHi | kNegLo) ^ sgn;
+  } else if (MU == 2) { // (-i h0, i h1)
+    g0 = swap_hl(h0) ^ kNegHi ^ sgn;
+    g1 = swap_hl(h1) ^ kNegLo ^ sgn;
+  } else {              // (h0, h1)
+    g0 = h0 ^ sgn;
+    g1 = h1 ^ sgn;
   }
-  float d[4];
-  mma_16816_like(a0, a1, b0, d);
-  // d = (re, im) of chi_{k=0}, chi_{k=1} at colour c; accumulate scale * chi
-  up[0] += s * d[0]; up[1] += s * d[1];
-  up[2] += s * d[2]; up[3] += s * d[3];
-  const float t = sg * s;
-  if (MU == 0) {        // e^+ chi = (-i chi_1, -i chi_0)
-    lo[0] += t * d[3]; lo[1] -= t * d[2];
-    lo[2] += t * d[1]; lo[3] -= t * d[0];
-  } else if (MU == 1) { // (chi_1, -chi_0)
-    lo[0] += t * d[2]; lo[1] += t * d[3];
-    lo[2] -= t * d[0]; lo[3] -= t * d[1];
-  } else if (MU == 2) { // (-i chi_0, i chi_1)
-    lo[0] += t * d[1]; lo[1] -= t * d[0];
-    lo[2] -= t * d[3]; lo[3] += t * d[2];
-  } else {              // (chi_0, chi_1)
-    lo[0] += t * d[0]; lo[1] += t * d[1];
-    lo[2] += t * d[2]; lo[3] += t * d[3];
-  }
+}
+
+// B fragment of lane (g, c): rows 2c, 2c+1, column g (colour a = g / 2, part g % 2)
+// of the real form of W = U (forward) or U^+ (backward).
+__device__ __forceinline__ uint32_t mma_link(const __half2* __restrict__ U16, long link, int g, int c, bool fwd) {
+  const int ca = g >> 1;
+  if (c == 3 || ca == 3) return 0u;
+  // W_ab = U_ab (forward) or conj(U_ba) (backward), a = ca, b = c
+  const uint32_t e = h2u(__ldg(U16 + link * 9 + (fwd ? ca * 3 + c : c * 3 + ca)));
+  if (g & 1) return fwd ? swap_hl(e) : (swap_hl(e) ^ kNegLo);    // (Im W, Re W)
+  return fwd ? (e ^ kNegHi) : e;                                   // (Re W, -Im W)
 }
 
 template <int EPI>
@@ -732,39 +727,92 @@ __global__ void hop_mma_kernel(FastArgs<__half, float> a, Tiling tl) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* sA = reinterpret_cast<float*>(smem_raw);
   const Thr t = thread_of(a, tl);
-  const int upb = a.L5 * a.N;                      // units per site (rt == N)
   const int nthr = blockDim.x * blockDim.y * blockDim.z;
-  const int lane = t.tid & 31, warp = t.tid >> 5, nwarp = (nthr + 31) >> 5;
+  Site* sSite = reinterpret_cast<Site*>(smem_raw + (size_t)nthr * kPadF * sizeof(float));
+  const int upb = a.L5 * a.N;                      // units per site (rt == N)
+  const int lane = t.tid & 31, warp = t.tid >> 5, nwarp = nthr >> 5;
   const int g = lane >> 2, c = lane & 3;
   const long h0 = (long)blockIdx.x * tl.nsb;
-  const int ntile = (tl.nsb * upb) >> 3;
+  if (t.tid < tl.nsb && h0 + t.tid < a.g.Vh) sSite[t.tid] = make_site(a.g, a.out_par, h0 + t.tid);
+  __syncthreads();
+  const uint4* in4 = reinterpret_cast<const uint4*>(a.in);
+  const int ntile = (tl.nsb * upb) >> 4;
+  const bool dag = a.dagger != 0;
   for (int tile = warp; tile < ntile; tile += nwarp) {
-    const int ub = tile * 8 + g;                   // unit of this lane within the block
-    const int site_l = ub / upb, lu = ub - site_l * upb;
-    const long h = h0 + site_l;
-    float up[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
-    // the 8 units of a tile share one site (upb % 8 == 0); out-of-range tiles skip as a whole warp
-    const bool site_ok = (h0 + ((tile * 8) / upb)) < a.g.Vh;
-    const int rr = lu % a.N;
-    if (site_ok) {
-      const Site x = make_site(a.g, a.out_par, h);
-      mma_term<0, true>(a, x, h, lu, upb, g, c, up, lo);
-      mma_term<0, false>(a, x, h, lu, upb, g, c, up, lo);
-      mma_term<1, true>(a, x, h, lu, upb, g, c, up, lo);
-      mma_term<1, false>(a, x, h, lu, upb, g, c, up, lo);
-      mma_term<2, true>(a, x, h, lu, upb, g, c, up, lo);
-      mma_term<2, false>(a, x, h, lu, upb, g, c, up, lo);
-      mma_term<3, true>(a, x, h, lu, upb, g, c, up, lo);
-      mma_term<3, false>(a, x, h, lu, upb, g, c, up, lo);
+    const int j = (tile << 4) / upb;
+    const long h = h0 + j;
+    if (h >= a.g.Vh) continue;                     // the whole warp skips together
+    const Site x = sSite[j];
+    const int lu0 = (tile << 4) - j * upb + g, lu1 = lu0 + 8;
+    int hn[8];
+    hn[0] = nbr_half<0, true>(a.g, x); hn[1] = nbr_half<0, false>(a.g, x);
+    hn[2] = nbr_half<1, true>(a.g, x); hn[3] = nbr_half<1, false>(a.g, x);
+    hn[4] = nbr_half<2, true>(a.g, x); hn[5] = nbr_half<2, false>(a.g, x);
+    hn[6] = nbr_half<3, true>(a.g, x); hn[7] = nbr_half<3, false>(a.g, x);
+    // neighbour scales (with the time boundary phase) and their largest magnitude per unit
+    float s0[8], s1[8];
+    float m0 = 0.f, m1 = 0.f;
+#pragma unroll
+    for (int d = 0; d < 8; d++) {
+      s0[d] = __ldg(a.in_nrm + (long)hn[d] * upb + lu0);
+      s1[d] = __ldg(a.in_nrm + (long)hn[d] * upb + lu1);
+      m0 = fmaxf(m0, s0[d]);
+      m1 = fmaxf(m1, s1[d]);
+    }
+    const bool tf = a.antiperiodic && x.c[3] == a.g.L[3] - 1, tb = a.antiperiodic && x.c[3] == 0;
+    const float i0 = m0 > 0.f ? 1.f / m0 : 0.f, i1 = m1 > 0.f ? 1.f / m1 : 0.f;
+    float up0[4] = {0.f, 0.f, 0.f, 0.f}, up1[4] = {0.f, 0.f, 0.f, 0.f};
+    float lo0[4] = {0.f, 0.f, 0.f, 0.f}, lo1[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int mu = 0; mu < 4; mu++) {
+      uint32_t ah0[4] = {0u, 0u, 0u, 0u}, ah1[4] = {0u, 0u, 0u, 0u};   // A for up_k0, up_k1
+      uint32_t ag0[4] = {0u, 0u, 0u, 0u}, ag1[4] = {0u, 0u, 0u, 0u};   // A for lo_k0, lo_k1
+#pragma unroll
+      for (int fb = 0; fb < 2; fb++) {
+        const int d = 2 * mu + fb;
+        const bool fwd = fb == 0;
+        // forward term uses sg = -1 (dagger: +1), backward the opposite
+        const bool neg_sg = fwd ? !dag : dag;
+        float r0 = s0[d] * i0, r1 = s1[d] * i1;
+        if (mu == 3 && (fwd ? tf : tb)) { r0 = -r0; r1 = -r1; }
+        if (c < 3) {
+          const uint4 q0 = __ldg(in4 + ((long)hn[d] * upb + lu0) * 3 + c);
+          const uint4 q1 = __ldg(in4 + ((long)hn[d] * upb + lu1) * 3 + c);
+          const __half2 rr0 = __float2half2_rn(r0), rr1 = __float2half2_rn(r1);
+          uint32_t x0, x1, y0, y1, z0, z1, w0, w1;
+          if (mu == 0) { mma_project<0>(q0, rr0, neg_sg, x0, x1, y0, y1); mma_project<0>(q1, rr1, neg_sg, z0, z1, w0, w1); }
+          else if (mu == 1) { mma_project<1>(q0, rr0, neg_sg, x0, x1, y0, y1); mma_project<1>(q1, rr1, neg_sg, z0, z1, w0, w1); }
+          else if (mu == 2) { mma_project<2>(q0, rr0, neg_sg, x0, x1, y0, y1); mma_project<2>(q1, rr1, neg_sg, z0, z1, w0, w1); }
+          else { mma_project<3>(q0, rr0, neg_sg, x0, x1, y0, y1); mma_project<3>(q1, rr1, neg_sg, z0, z1, w0, w1); }
+          // rows g (unit lu0) and g + 8 (unit lu1); columns of this direction half: 2 fb
+          ah0[2 * fb] = x0; ah0[2 * fb + 1] = z0;
+          ah1[2 * fb] = x1; ah1[2 * fb + 1] = z1;
+          ag0[2 * fb] = y0; ag0[2 * fb + 1] = w0;
+          ag1[2 * fb] = y1; ag1[2 * fb + 1] = w1;
+        }
+      }
+      const long lf = ((long)a.out_par * a.g.Vh + h) * 4 + mu;
+      const long lb = ((long)(1 - a.out_par) * a.g.Vh + hn[2 * mu + 1]) * 4 + mu;
+      const uint32_t bf = mma_link(a.U16, lf, g, c, true);
+      const uint32_t bb = mma_link(a.U16, lb, g, c, false);
+      mma_m16n8k16(ah0, bf, bb, up0);
+      mma_m16n8k16(ah1, bf, bb, up1);
+      mma_m16n8k16(ag0, bf, bb, lo0);
+      mma_m16n8k16(ag1, bf, bb, lo1);
     }
     if (c < 3) {
-      const bool live = site_ok && (a.active == nullptr || a.active[rr] != 0);
-      float* row = sA + (size_t)ub * kPadF + 2 * c;
-      // spins 0, 1 (upper) and 2, 3 (lower) of colour c
-      row[0] = live ? up[0] : 0.f;  row[1] = live ? up[1] : 0.f;
-      row[6] = live ? up[2] : 0.f;  row[7] = live ? up[3] : 0.f;
-      row[12] = live ? lo[0] : 0.f; row[13] = live ? lo[1] : 0.f;
-      row[18] = live ? lo[2] : 0.f; row[19] = live ? lo[3] : 0.f;
+      // C row g = unit lu0 (entries 0, 1), row g + 8 = unit lu1 (entries 2, 3); columns 2c, 2c+1 = colour c
+      const int ub0 = (tile << 4) + g, ub1 = ub0 + 8;
+      const int rr0 = lu0 % a.N, rr1 = lu1 % a.N;
+      const bool live0 = a.active == nullptr || a.active[rr0] != 0;
+      const bool live1 = a.active == nullptr || a.active[rr1] != 0;
+      const float f0 = live0 ? m0 : 0.f, f1 = live1 ? m1 : 0.f;
+      float* r0p = sA + (size_t)ub0 * kPadF + 2 * c;
+      float* r1p = sA + (size_t)ub1 * kPadF + 2 * c;
+      r0p[0] = f0 * up0[0]; r0p[1] = f0 * up0[1]; r0p[6] = f0 * up1[0]; r0p[7] = f0 * up1[1];
+      r0p[12] = f0 * lo0[0]; r0p[13] = f0 * lo0[1]; r0p[18] = f0 * lo1[0]; r0p[19] = f0 * lo1[1];
+      r1p[0] = f1 * up0[2]; r1p[1] = f1 * up0[3]; r1p[6] = f1 * up1[2]; r1p[7] = f1 * up1[3];
+      r1p[12] = f1 * lo0[2]; r1p[13] = f1 * lo0[3]; r1p[18] = f1 * lo1[2]; r1p[19] = f1 * lo1[3];
     }
   }
   __syncthreads();
@@ -779,7 +827,7 @@ template <int EPI>
 cudaError_t launch_mma_one(const FastArgs<__half, float>& a, const Tiling& t, cudaStream_t st) {
   const dim3 grid((unsigned)t.ntiles, (unsigned)t.ngroups);
   const dim3 block((unsigned)t.rt, (unsigned)a.L5, (unsigned)t.nsb);
-  size_t smem = (size_t)t.threads * kPadF * sizeof(float);
+  size_t smem = (size_t)t.threads * kPadF * sizeof(float) + (size_t)t.nsb * sizeof(Site);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(hop_mma_kernel<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -822,7 +870,21 @@ int fast_max_threads() {
 
 bool mma_hop_usable(const Tiling& t, int L5, int N) {
   const int upb = L5 * N;
-  return t.rt == N && t.ngroups == 1 && upb % 8 == 0;
+  // whole sites per block, 16-unit tiles inside one site, whole warps
+  return t.rt == N && t.ngroups == 1 && upb % 16 == 0 && t.threads % 32 == 0;
+}
+
+int mma_max_threads() {
+  int m = 1024;
+  const void* ks[] = {(const void*)hop_mma_kernel<E_RAW>, (const void*)hop_mma_kernel<E_BAINV>,
+                      (const void*)hop_mma_kernel<E_AINVD_BD>, (const void*)hop_mma_kernel<E_A_SAME>,
+                      (const void*)hop_mma_kernel<E_AD_SAME_BD>, (const void*)hop_mma_kernel<E_AINV_SAME>};
+  for (const void* k : ks) {
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, k) != cudaSuccess) return 128;
+    if (fa.maxThreadsPerBlock < m) m = fa.maxThreadsPerBlock;
+  }
+  return m;
 }
 
 cudaError_t launch_fast_mma(const FastArgs<__half, float>& a, const Tiling& t, int epi, cudaStream_t st) {

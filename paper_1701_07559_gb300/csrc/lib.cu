@@ -454,12 +454,18 @@ void choose_hop(FastOp<S, T>& op, const Cfg* cfg, int nsb_req, int variant, cons
   op.mma = false;
   op.stage = nullptr;
   op.U16 = cfg->U16;
-  if (variant == HOP_MMA && std::is_same<S, __half>::value && upb % 8 == 0 && upb <= 1024 && cfg->U16) {
-    int nsb = nsb_req > 0 ? nsb_req : (128 / upb > 1 ? 128 / upb : 1);
-    if (nsb > 64) nsb = 64;
-    while (nsb > 1 && nsb * upb > 1024) nsb--;
-    op.tl = make_tiling(g.Vh, L5, N, nsb, nsb * upb);
-    if (mma_hop_usable(op.tl, L5, N)) { op.mma = true; return; }
+  if (variant == HOP_MMA && std::is_same<S, __half>::value && upb % 16 == 0 && cfg->U16) {
+    // whole sites per block and a whole number of warps: nsb a multiple of 32 / gcd(upb, 32)
+    int gcd = upb, b = 32;
+    while (b) { int r = gcd % b; gcd = b; b = r; }
+    const int step = 32 / gcd;
+    int nsb = step;
+    while (nsb * upb < 128) nsb += step;
+    if (nsb_req > 0 && nsb_req % step == 0) nsb = nsb_req;
+    if (nsb <= 64 && nsb * upb <= mma_max_threads()) {
+      op.tl = make_tiling(g.Vh, L5, N, nsb, nsb * upb);
+      if (mma_hop_usable(op.tl, L5, N)) { op.mma = true; return; }
+    }
   }
   op.tl = fast_tiling<S>(g, L5, N, nsb_req, &staged, variant == HOP_STAGED);
   op.stage = staged ? stage : nullptr;
@@ -1124,7 +1130,7 @@ int schur_batch_impl(mdwf_ctx* ctx, Cfg* cfg, int n, const double* const* in, do
   si.budget = wait_budget(ctx->device, 2.0);
   si.extra_tx = 0;
   si.err = errw;
-  choose_hop(op, cfg, 0, flags, &si);
+  choose_hop(op, cfg, (flags >> 8) & 0xff, flags & 0xff, &si);
   Tiling tb = make_tiling(g.Vh, L5, N, 2, 1024);
   F<S> fin, fu, ft, fo;
   CK(ws_field<S>(ctx, "sb.in", units, &fin));

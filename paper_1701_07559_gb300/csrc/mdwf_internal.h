@@ -6,6 +6,10 @@
 //                                                 24 = [spin 4][colour 3][re, im]
 //   16-bit storage adds a scale per (h, s, r):   nrm[h][s][r] (float); the stored
 //                                                 values are v / nrm, nrm = max |v|.
+//   fp16 storage orders the 24 reals of a unit colour-major, [colour][spin][re,im],
+//   so that the four spins of one colour are one 16-byte word (the tensor-core hop
+//   loads them per lane); every other type, and every register copy, uses
+//   [spin][colour][re,im].
 //   gauge field:                [parity][h][mu][18]   (3x3 complex, row major),
 //                                mu = 0..3 for x, y, z, t; U_mu(x) of the site x;
 //                                the FP32 copy pads each link to 20 floats.
@@ -81,13 +85,13 @@ __device__ __forceinline__ void load24<float, float>(const float* __restrict__ v
 template <>
 __device__ __forceinline__ void load24<__half, float>(const __half* __restrict__ v, const float* __restrict__ nrm, long u, float a[24]) {
   const uint4* p = reinterpret_cast<const uint4*>(v + 24 * u);
-  float s = __ldg(nrm + u);
+  const float s = __ldg(nrm + u);
 #pragma unroll
-  for (int i = 0; i < 3; i++) {
-    uint4 t = __ldg(p + i);
+  for (int c = 0; c < 3; c++) {           // word c: spins 0..3 of colour c
+    uint4 t = __ldg(p + c);
     const __half2* hh = reinterpret_cast<const __half2*>(&t);
 #pragma unroll
-    for (int j = 0; j < 4; j++) { float2 f = __half22float2(hh[j]); a[8*i+2*j] = f.x * s; a[8*i+2*j+1] = f.y * s; }
+    for (int k = 0; k < 4; k++) { float2 f = __half22float2(hh[k]); a[6*k+2*c] = f.x * s; a[6*k+2*c+1] = f.y * s; }
   }
 }
 template <>
@@ -130,12 +134,12 @@ __device__ __forceinline__ void store24<__half, float>(__half* __restrict__ v, f
   nrm[u] = m;
   uint4* p = reinterpret_cast<uint4*>(v + 24 * u);
 #pragma unroll
-  for (int i = 0; i < 3; i++) {
+  for (int c = 0; c < 3; c++) {
     uint4 t;
     __half2* hh = reinterpret_cast<__half2*>(&t);
 #pragma unroll
-    for (int j = 0; j < 4; j++) hh[j] = __floats2half2_rn(a[8*i+2*j] * inv, a[8*i+2*j+1] * inv);
-    p[i] = t;
+    for (int k = 0; k < 4; k++) hh[k] = __floats2half2_rn(a[6*k+2*c] * inv, a[6*k+2*c+1] * inv);
+    p[c] = t;
   }
 }
 template <>
@@ -172,14 +176,14 @@ __device__ __forceinline__ void load_part<float, float>(const float* __restrict_
 template <>
 __device__ __forceinline__ void load_part<__half, float>(const __half* __restrict__ v, const float* __restrict__ nrm,
                                                          long u, int part, float* o) {
-  const uint2* p = reinterpret_cast<const uint2*>(v + 24 * u + 12 * part);
+  // colour-major storage: spins 2 part, 2 part + 1 of colour c are the 8 bytes at 16 c + 8 part
   const float s = __ldg(nrm + u);
 #pragma unroll
-  for (int i = 0; i < 3; i++) {
-    uint2 t = __ldg(p + i);
+  for (int c = 0; c < 3; c++) {
+    uint2 t = __ldg(reinterpret_cast<const uint2*>(v + 24 * u + 8 * c + 4 * part));
     const __half2* hh = reinterpret_cast<const __half2*>(&t);
     float2 a = __half22float2(hh[0]), b = __half22float2(hh[1]);
-    o[4*i] = a.x * s; o[4*i+1] = a.y * s; o[4*i+2] = b.x * s; o[4*i+3] = b.y * s;
+    o[2*c] = a.x * s; o[2*c+1] = a.y * s; o[6+2*c] = b.x * s; o[6+2*c+1] = b.y * s;
   }
 }
 template <>
@@ -214,11 +218,11 @@ template <>
 __device__ __forceinline__ void load24_smem<__half, float>(const __half* p, float a[24]) {
   const uint4* q = reinterpret_cast<const uint4*>(p);
 #pragma unroll
-  for (int i = 0; i < 3; i++) {
-    uint4 t = q[i];
+  for (int c = 0; c < 3; c++) {
+    uint4 t = q[c];
     const __half2* hh = reinterpret_cast<const __half2*>(&t);
 #pragma unroll
-    for (int j = 0; j < 4; j++) { float2 f = __half22float2(hh[j]); a[8*i+2*j] = f.x; a[8*i+2*j+1] = f.y; }
+    for (int k = 0; k < 4; k++) { float2 f = __half22float2(hh[k]); a[6*k+2*c] = f.x; a[6*k+2*c+1] = f.y; }
   }
 }
 template <>
@@ -348,6 +352,7 @@ cudaError_t launch_fast(const FastArgs<S, T>& a, const Tiling& t, int epi, cudaS
                         const StageInfo* stage = nullptr);
 // Tensor-core hop (fp16 storage): usable when a block holds whole sites and L5 N % 8 == 0.
 bool mma_hop_usable(const Tiling& t, int L5, int N);
+int mma_max_threads();
 cudaError_t launch_fast_mma(const FastArgs<__half, float>& a, const Tiling& t, int epi, cudaStream_t st);
 // Shared-memory bytes of a staged launch (0 if the tiling cannot be staged).
 template <typename S, typename T>

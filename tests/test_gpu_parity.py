@@ -251,9 +251,10 @@ def test_bounded_wait_reports_timeout_and_context_survives():
 
 @pytest.mark.parametrize('precision,tol', [('double', 1e-13), ('single', 2e-6), ('half', 4e-3), ('bf16', 3e-2)])
 @pytest.mark.parametrize('dagger', [0, 1])
-@pytest.mark.parametrize('variant', [0, 1, 2])
+@pytest.mark.parametrize('variant', [0, 1, 2, 3])
 @pytest.mark.parametrize('L5,masses', [(5, [0.05, 0.01, 0.2, 0.0022, 0.1]),            # L5 N = 25
-                                       (4, [0.05, 0.01, 0.2, 0.0022, 0.1, 0.3])])      # L5 N = 24: tensor-core tiles
+                                       (4, [0.05, 0.01, 0.2, 0.0022]),                 # L5 N = 16: tensor-core tiles
+                                       (6, [0.05, 0.01, 0.2, 0.0022, 0.1, 0.3, 0.02, 0.07])])   # L5 N = 48
 def test_schur_batch_multi_rhs(precision, tol, dagger, variant, L5, masses):
     """The batched Schur operator (the solver's kernels, N RHS with different masses,
     every hop variant) against the oracle, slot by slot."""
