@@ -41,12 +41,18 @@ def parse():
     ap.add_argument('--no-fp64', action='store_true', help='skip the FP64 single-RHS GPU CG comparison')
     ap.add_argument('--no-cpu', action='store_true', help='skip the oracle cpu_baseline sample')
     ap.add_argument('--rhs', type=int, default=12, help='spin-colour sources per step (12 = the workload)')
-    ap.add_argument('--mode', default='solve', choices=['solve', 'op'],
+    ap.add_argument('--mode', default='solve', choices=['solve', 'op', 'serve'],
                     help="'op': only apply the batched Schur operator (the solver's hop kernels), for profiling")
     ap.add_argument('--lattice', default=None, help="op mode: Lx,Ly,Lz,Lt instead of the workload's 16,16,16,48")
     ap.add_argument('--hop-variant', type=int, default=0,
                     help='0 automatic, 1 CUDA-core direct loads, 2 CUDA-core staged, 3 tensor-core (fp16)')
     ap.add_argument('--nsb', type=int, default=0, help='sites per thread block (0: chosen by the library)')
+    ap.add_argument('--requests', type=int, default=300, help='serve mode: requests per arrival rate')
+    ap.add_argument('--rates', default='0.5,0.9,1.2', help='serve mode: arrival rates as fractions of capacity')
+    ap.add_argument('--serve-lattices', default='16,16,16,48:12;24,24,24,64:8;32,32,32,96:6',
+                    help='serve mode: the resident configurations, Lx,Ly,Lz,Lt:L5 separated by ;')
+    ap.add_argument('--slots', type=int, default=12, help='serve mode: maximum slots of one session')
+    ap.add_argument('--hbm-budget-gb', type=float, default=0.0, help='serve mode: HBM budget (0: 85%% of free)')
     return ap.parse_args()
 
 
@@ -406,12 +412,99 @@ def run_op(args):
     return 0
 
 
+# the serving mix: three resident flowed configurations (seeds 5, 6, 7); the
+# 24^3 x 64 one carries the a12m310 action of Table II, the others the a15m310 one
+SERVE_ACTIONS = {12: (1.3, 1.5, 0.5), 8: (1.2, 1.25, 0.25), 6: (1.3, 1.5, 0.5)}
+SERVE_MASSES = (0.0102, 0.0158, 0.0216)
+
+
+def serve_requests(serving, names, dims, n, seed):
+    """n requests: configuration and mass uniform, Z2 noise or point source 50/50."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        k = int(rng.integers(len(names)))
+        mass = float(SERVE_MASSES[int(rng.integers(3))])
+        if rng.random() < 0.5:
+            src = ('z2', int(rng.integers(1 << 62)))
+        else:
+            src = ('point', int(rng.integers(4)), int(rng.integers(3)), tuple(int(rng.integers(d)) for d in dims[k]))
+        out.append(serving.Request(names[k], mass, src))
+    return out
+
+
+def run_serve(args):
+    """Continuous-batching serving of a Poisson stream of solve requests over the
+    resident configurations: capacity from a closed-loop run, then p50/p99 latency
+    and solves/s at the given fractions of it."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import synth
+    from paper_1701_07559_gb300 import serving
+    torch.cuda.set_device(0)
+    budget = int(args.hbm_budget_gb * 1e9) if args.hbm_budget_gb > 0 else None
+    srv = serving.Server(device=0, hbm_budget=budget, tol=1e-10, precision=args.precision, max_slots=args.slots)
+    names, dims = [], []
+    t0 = time.perf_counter()
+    for i, spec in enumerate(args.serve_lattices.split(';')):
+        lat, l5 = spec.split(':')
+        d = tuple(int(v) for v in lat.split(','))
+        l5 = int(l5)
+        M5, b5, c5 = SERVE_ACTIONS.get(l5, (1.3, 1.5, 0.5))
+        U = synth.flowed_gauge(d, 5 + i, 0.4, 1.0, 0.01)
+        name = '%dx%dx%dx%d L5=%d' % (d + (l5,))
+        srv.add_config(name, d, U, M5, b5, c5, SERVE_MASSES[1], l5)
+        names.append(name)
+        dims.append(d)
+    setup_s = time.perf_counter() - t0
+    # warm-up: one request per configuration (sessions, graphs)
+    srv.run(serve_requests(serving, names, dims, 2 * len(names), 1))
+    # capacity: everything queued at once
+    ncap = max(2 * args.slots, args.requests // 3)
+    clocks = ClockSampler(0)
+    clocks.start()
+    done = srv.run(serve_requests(serving, names, dims, ncap, 7))
+    cap = serving.Server.metrics(done)
+    capacity = cap['solves_per_s']
+    runs = []
+    for j, frac in enumerate(float(f) for f in args.rates.split(',')):
+        reqs = serve_requests(serving, names, dims, args.requests, 8 + j)
+        arr = serving.poisson_arrivals(len(reqs), frac * capacity, 8 + j)
+        done = srv.run(reqs, arr)
+        m = serving.Server.metrics(done)
+        m['rate_fraction'] = frac
+        m['offered_per_s'] = frac * capacity
+        m['per_config'] = {}
+        for name in names:
+            sub = [r for r in done if r.config == name]
+            if sub:
+                mm = serving.Server.metrics(sub)
+                m['per_config'][name] = {'requests': len(sub), 'p50_s': mm['p50_s'], 'p99_s': mm['p99_s'],
+                                         'iters_mean': mm['iters_mean']}
+        runs.append(m)
+    clk = clocks.stop()
+    peak_bytes = max(s[3] for s in srv.samples)
+    queue_max = max(s[1] for s in srv.samples)
+    srv.close()
+    print(json.dumps({'mode': 'serve', 'metric': 'p50/p99 latency and solves/s of a Poisson stream of solves to 1e-10',
+                      'precision': args.precision, 'configs': names, 'masses': SERVE_MASSES,
+                      'sources': 'Z2 noise or point, 50/50', 'slots_max': args.slots,
+                      'hbm_budget_bytes': srv.budget, 'hbm_peak_accounted_bytes': peak_bytes, 'queue_max': queue_max,
+                      'capacity_solves_per_s': capacity, 'capacity_run': cap, 'runs': runs, 'setup_s': setup_s,
+                      'clocks': clk, 'data': 'synthetic'}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == 'reference':
         return run_reference(args)
     if args.mode == 'op':
         return run_op(args)
+    if args.mode == 'serve':
+        return run_serve(args)
     return run_ours(args)
 
 

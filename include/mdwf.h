@@ -48,6 +48,7 @@ extern "C" {
 #define MDWF_ERR_TIMEOUT (-5)       /* a bounded device wait ran out */
 #define MDWF_ERR_CUDA (-6)          /* a CUDA runtime call failed */
 #define MDWF_ERR_STATE (-7)         /* gauge field or action not set for this cfg_id */
+#define MDWF_ERR_FULL (-8)          /* a session has no free slot */
 
 /* Storage precision of the inner (sloppy) solver vectors.  Arithmetic is FP64
  * for MDWF_PREC_DOUBLE and FP32 otherwise; the solution accumulator, the
@@ -214,6 +215,56 @@ int mdwf_apply_schur_batch_dev_noalloc(mdwf_ctx* ctx, int cfg_id, int n, const d
 int mdwf_apply_dslash_dev(mdwf_ctx* ctx, int cfg_id, const double* in, double* out, int out_parity, int dagger,
                           void* stream);
 int mdwf_apply_mdwf_dev(mdwf_ctx* ctx, int cfg_id, const double* in, double* out, int dagger, void* stream);
+
+/* ---- Solver sessions: continuous batching --------------------------------
+ * A session keeps the device state of `slots` right-hand sides of one gauge
+ * configuration resident.  Requests (a 5D source, a quark mass, an output field,
+ * a caller tag) enter free slots between CG chunks; every chunk advances all
+ * occupied slots in the same kernel launches; converged slots are reconstructed,
+ * checked in FP64 and written to their output field, and become free again.
+ * This is the serving loop of the batched solve (the paper's propagator solves,
+ * Sec. VII, as requests); a request gives the same x alone as in any mix.
+ * All pointers are device fields in the API layout; calls on one session come
+ * from one host thread.  Sessions of different contexts run on their own
+ * streams and overlap on the device. */
+typedef struct mdwf_session mdwf_session;
+
+/* Device bytes a session of `slots` slots holds (for admission control), or -1. */
+long long mdwf_session_bytes(mdwf_ctx* ctx, int cfg_id, int slots, int precision);
+
+/* Create a session on `stream` (NULL: the context's stream) with the solver
+ * options (precision, delta, chunk, max_iter, ...) and tolerance of every solve.
+ * Errors: ARG, STATE, NOMEM, CUDA. */
+int mdwf_session_create(mdwf_ctx* ctx, int cfg_id, int slots, const mdwf_solver_opts* opts, double tol, void* stream,
+                        mdwf_session** out);
+int mdwf_session_destroy(mdwf_session* s);
+
+/* Put a request into a free slot (returned in *slot): source src5d (read now),
+ * quark mass, solution field x5d (written when the request completes), tag.
+ * Errors: FULL (no free slot), ARG, NONFINITE, CUDA. */
+int mdwf_session_submit(mdwf_session* s, const double* src5d, double mass, double* x5d, long long tag, int* slot);
+
+/* Enqueue `iters` CG iterations (0: opts.chunk) of every occupied slot on the
+ * session's stream and return without waiting. */
+int mdwf_session_launch(mdwf_session* s, int iters);
+
+/* Wait for the session's work, run its reliable updates, and complete up to
+ * max_done converged slots (tags[] and stats[] receive them, *n_done their number;
+ * stats.time_s is the time since submit).  Errors: CUDA, TIMEOUT. */
+int mdwf_session_poll(mdwf_session* s, int max_done, long long* tags, mdwf_solve_stats* stats, int* n_done);
+
+/* Number of occupied slots. */
+int mdwf_session_occupied(const mdwf_session* s);
+
+/* mdwf_make_source on device fields (eta4d: V * 24 doubles; src5d: L5 * V * 24), on `stream`. */
+int mdwf_make_source_dev(mdwf_ctx* ctx, int cfg_id, const double* eta4d, double* src5d, void* stream);
+
+/* Z2 noise 4D source on a device field eta4d (V * 24 doubles), on `stream`:
+ * complex element k ([t][z][y][x][spin][colour] order) is +1 or -1 (imaginary
+ * part 0) by the top bit of the k-th output of SplitMix64 started from `seed`
+ * (Steele, Lea and Flood, OOPSLA 2014).  A synthetic input for serving
+ * workloads; the paper's own sources (Sec. III) are smeared point sources. */
+int mdwf_z2_source_dev(mdwf_ctx* ctx, unsigned long long seed, double* eta4d, void* stream);
 
 /* 4D propagator from a 5D solution: q = P_- x_0 + P_+ x_{L5-1} (host arrays;
  * x5d has L5 * V * 24 doubles, q4d V * 24).  Pure host code.  Errors: ARG. */

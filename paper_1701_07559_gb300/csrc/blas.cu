@@ -257,6 +257,46 @@ __global__ void k_xpay_b(const S* __restrict__ r, const float* __restrict__ r_nr
   store24<S, T>(uv, u_nrm, x.u, y);
 }
 
+// Zero the units of the slots in mask.
+template <typename S>
+__global__ void k_zero_masked(S* __restrict__ v, float* __restrict__ nrm, Tiling tl, long Vh, int L5, int N,
+                              const int* __restrict__ mask) {
+  using T = typename StoreTraits<S>::T;
+  Unit x = unit_of(tl, Vh, L5, N);
+  if (!x.valid || !mask[x.r]) return;
+  T z[24];
+#pragma unroll
+  for (int i = 0; i < 24; i++) z[i] = 0;
+  store24<S, T>(v, nrm, x.u, z);
+}
+
+// Wall source of a 4D field (API layout): slice 0 gets the P_+ spins (0, 1),
+// slice L5-1 the P_- spins (2, 3); the other slices must already be zero.
+__global__ void k_walls(const double* __restrict__ eta, double* __restrict__ w, long V, int L5) {
+  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= V * 24) return;
+  const int k = (int)(i % 24);
+  const int spin = k / 6;
+  if (spin < 2) w[i] = eta[i];
+  else w[(long)(L5 - 1) * V * 24 + i] = eta[i];
+}
+
+// Z2 noise source: complex element k of a 4D field ([t][z][y][x][spin][colour],
+// k = 0 .. 12V-1) is (+1, 0) or (-1, 0) by the top bit of the k-th output of
+// SplitMix64 from state `seed` (Steele, Lea and Flood, OOPSLA 2014): the state
+// advances by the 64-bit golden-ratio increment and each output is the state
+// passed through the 64-bit mixing finaliser of that generator.
+__global__ void k_z2(unsigned long long seed, double* __restrict__ eta, long n) {
+  long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  unsigned long long z = seed + (unsigned long long)(k + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z = z ^ (z >> 31);
+  eta[2 * k] = (z >> 63) ? -1.0 : 1.0;
+  eta[2 * k + 1] = 0.0;
+}
+
 // rho = S(bhat - q) with bhat in FP64 and q in FP32 (the residual of a reliable
 // update computed with FP32 arithmetic); partial |bhat - q|^2 in FP64.
 template <typename S>
@@ -369,6 +409,24 @@ cudaError_t resid_update(const double* bhat, const float* q, S* rho, float* rho_
   return cudaGetLastError();
 }
 
+template <typename S>
+cudaError_t zero_masked(S* v, float* nrm, const Tiling& t, long Vh, int L5, int N, const int* mask, cudaStream_t st) {
+  k_zero_masked<S><<<tile_grid(t), t.threads, 0, st>>>(v, nrm, t, Vh, L5, N, mask);
+  return cudaGetLastError();
+}
+
+cudaError_t walls(const double* eta, double* w, long V, int L5, cudaStream_t st) {
+  long n = V * 24;
+  k_walls<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(eta, w, V, L5);
+  return cudaGetLastError();
+}
+
+cudaError_t z2_source(unsigned long long seed, double* eta, long V, cudaStream_t st) {
+  const long n = V * 12;
+  k_z2<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(seed, eta, n);
+  return cudaGetLastError();
+}
+
 cudaError_t finalize(const double* partials, long ntiles, int N, double* out, cudaStream_t st) {
   k_finalize<<<N, 256, 0, st>>>(partials, ntiles, N, out);
   return cudaGetLastError();
@@ -391,6 +449,12 @@ cudaError_t finalize(const double* partials, long ntiles, int N, double* out, cu
                                  cudaStream_t);                                                                    \
   template cudaError_t resid_update<S>(const double*, const float*, S*, float*, const Tiling&, long, int, int,      \
                                        const int*, double*, cudaStream_t);
+template cudaError_t zero_masked<double>(double*, float*, const Tiling&, long, int, int, const int*, cudaStream_t);
+template cudaError_t zero_masked<float>(float*, float*, const Tiling&, long, int, int, const int*, cudaStream_t);
+template cudaError_t zero_masked<__half>(__half*, float*, const Tiling&, long, int, int, const int*, cudaStream_t);
+template cudaError_t zero_masked<__nv_bfloat16>(__nv_bfloat16*, float*, const Tiling&, long, int, int, const int*,
+                                                cudaStream_t);
+
 MDWF_INST_B(double)
 MDWF_INST_B(float)
 MDWF_INST_B(__half)

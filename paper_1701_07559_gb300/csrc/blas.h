@@ -46,6 +46,12 @@ template <typename S>
 cudaError_t resid_update(const double* bhat, const float* q, S* rho, float* rho_nrm, const Tiling& t, long Vh, int L5,
                          int N, const int* mask, double* partials, cudaStream_t st);
 
+template <typename S>
+cudaError_t zero_masked(S* v, float* nrm, const Tiling& t, long Vh, int L5, int N, const int* mask, cudaStream_t st);
+
+cudaError_t walls(const double* eta, double* w, long V, int L5, cudaStream_t st);
+cudaError_t z2_source(unsigned long long seed, double* eta, long V, cudaStream_t st);
+
 cudaError_t finalize(const double* partials, long ntiles, int N, double* out, cudaStream_t st);
 
 }  // namespace mdwf

@@ -50,6 +50,22 @@ struct mdwf_ctx {
   std::string err;
   cudaStream_t stream = nullptr;
   std::map<std::string, std::pair<void*, size_t>> ws;  // reusable device workspace
+  int next_session = 0;
+};
+
+struct SessionBase {
+  virtual ~SessionBase() {}
+  virtual int submit(const double* src, double mass, double* x, long long tag, int* slot) = 0;
+  virtual int launch(int iters) = 0;
+  virtual int poll(int max_done, long long* tags, mdwf_solve_stats* stats, int* n_done) = 0;
+  virtual int occupied() const = 0;
+};
+
+struct mdwf_session {
+  mdwf_ctx* ctx = nullptr;
+  SessionBase* impl = nullptr;
+  std::string prefix;
+  cudaStream_t stream = nullptr;
 };
 
 namespace {
@@ -570,6 +586,7 @@ struct BatchSolver {
   bool profiling = false;
   StageInfo stage;
   int* errw = nullptr;            // device status word of the bounded waits
+  std::string wsp;                // prefix of this solver's workspace names (sessions own theirs)
 
   ~BatchSolver() { if (graph) cudaGraphExecDestroy(graph); }
 
@@ -583,8 +600,8 @@ struct BatchSolver {
     const Geom& g = c->g;
     long units = g.Vh * L5 * N;
     cudaError_t e = cudaSuccess;
-    mass64 = (double*)ws_get(c, "mass64", sizeof(double) * N, &e); CK(e);
-    mass32 = (float*)ws_get(c, "mass32", sizeof(float) * N, &e); CK(e);
+    mass64 = (double*)ws_get(c, wsp + "mass64", sizeof(double) * N, &e); CK(e);
+    mass32 = (float*)ws_get(c, wsp + "mass32", sizeof(float) * N, &e); CK(e);
     std::vector<float> m32(masses.begin(), masses.end());
     CK(cudaMemcpyAsync(mass64, masses.data(), sizeof(double) * N, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(mass32, m32.data(), sizeof(float) * N, cudaMemcpyHostToDevice, st));
@@ -597,7 +614,7 @@ struct BatchSolver {
     opS.f = make_fifth<T>(cf->act, kFP64 ? (const T*)mass64 : (const T*)mass32);
     if (nsb * L5 > 1024) nsb = 1;
     tl_blas = make_tiling(g.Vh, L5, N, 2, kFP64 ? 512 : 1024);
-    errw = (int*)ws_get(c, "errw", sizeof(int), &e); CK(e);
+    errw = (int*)ws_get(c, wsp + "errw", sizeof(int), &e); CK(e);
     CK(cudaMemsetAsync(errw, 0, sizeof(int), st));
     stage.spin_bytes = stage.nrm_bytes = 0;
     stage.budget = wait_budget(c->device, o.wait_timeout_s > 0 ? o.wait_timeout_s : 2.0);
@@ -613,20 +630,20 @@ struct BatchSolver {
     if (profile) opS.prof = &prof;
     F<double>* f64[] = {&b_e, &b_o, &x_acc, &x_hi, &x_o, &bhat, &rho64, &u64, &t64};
     const char* n64[] = {"b_e", "b_o", "x_acc", "x_hi", "x_o", "bhat", "rho64", "u64", "t64"};
-    for (int i = 0; i < 9; i++) CK(ws_field<double>(c, n64[i], units, f64[i]));
+    for (int i = 0; i < 9; i++) CK(ws_field<double>(c, wsp + n64[i], units, f64[i]));
     if (!kFP64) {
       F<float>* f32[] = {&xf, &uf, &tf, &qf};
       const char* n32[] = {"xf", "uf", "tf", "qf"};
-      for (int i = 0; i < 4; i++) CK(ws_field<float>(c, n32[i], units, f32[i]));
+      for (int i = 0; i < 4; i++) CK(ws_field<float>(c, wsp + n32[i], units, f32[i]));
     }
     F<S>* fS[] = {&p, &u, &t, &q, &rho, &r};
     const char* nS[] = {"p", "u", "t", "q", "rho", "r"};
-    for (int i = 0; i < 6; i++) CK(ws_field<S>(c, std::string("S.") + nS[i], units, fS[i]));
-    CK(ws_field<SX>(c, "xlo", units, &xlo));
-    part = (double*)ws_get(c, "partials", sizeof(double) * g.Vh * N, &e); CK(e);
-    double* d = (double*)ws_get(c, "scal_d", sizeof(double) * 11 * N, &e); CK(e);
-    int* ip = (int*)ws_get(c, "scal_i", sizeof(int) * 3 * N, &e); CK(e);
-    umask_d = (int*)ws_get(c, "umask", sizeof(int) * N, &e); CK(e);
+    for (int i = 0; i < 6; i++) CK(ws_field<S>(c, wsp + "S." + nS[i], units, fS[i]));
+    CK(ws_field<SX>(c, wsp + "xlo", units, &xlo));
+    part = (double*)ws_get(c, wsp + "partials", sizeof(double) * g.Vh * N, &e); CK(e);
+    double* d = (double*)ws_get(c, wsp + "scal_d", sizeof(double) * 11 * N, &e); CK(e);
+    int* ip = (int*)ws_get(c, wsp + "scal_i", sizeof(int) * 3 * N, &e); CK(e);
+    umask_d = (int*)ws_get(c, wsp + "umask", sizeof(int) * N, &e); CK(e);
     sc.gamma = d; sc.gamma_prev = d + N; sc.alpha = d + 2 * N; sc.beta = d + 3 * N; sc.rho2 = d + 4 * N;
     sc.rho2_max = d + 5 * N; sc.stop2 = d + 6 * N; sc.qq = d + 7 * N; sc.rr = d + 8 * N; sc.tmp = d + 9 * N;
     sc.bhat2 = d + 10 * N;
@@ -980,6 +997,258 @@ int solve_dispatch(mdwf_ctx* ctx, int cfg_id, int n, const double* const* srcs, 
     case MDWF_PREC_HALF: return solve_batch_impl<__half>(ctx, cfg, n, srcs, m, xs, tol, o, stats, st);
     case MDWF_PREC_BF16: return solve_batch_impl<__nv_bfloat16>(ctx, cfg, n, srcs, m, xs, tol, o, stats, st);
     default: return fail(ctx, MDWF_ERR_ARG, "solve: unknown precision");
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Solver sessions: continuous batching
+// ---------------------------------------------------------------------------
+// A session owns the state of a batch of `slots` right-hand sides for one gauge
+// configuration.  Requests enter free slots between CG chunks (submit), every
+// chunk advances all occupied slots at once (launch), and poll() performs the
+// reliable updates and hands back the solutions of converged slots, freeing
+// them for new requests.  A slot always enters at a chunk boundary and every
+// per-slot operation is independent of the other slots, so a request follows
+// the same arithmetic alone as in any mix.
+
+template <typename S>
+struct SessionImpl : SessionBase {
+  mdwf_ctx* ctx;
+  Cfg* cfg;
+  BatchSolver<S> sv;
+  int N = 0;
+  double tol = 1e-10;
+  mdwf_solver_opts o;
+  cudaStream_t st = nullptr;
+  std::vector<double> masses;
+  std::vector<int> used, nupd;
+  std::vector<long long> tags;
+  std::vector<double*> outs;
+  std::vector<double> b2;
+  std::vector<std::chrono::steady_clock::time_point> t0;
+  int* fmask = nullptr;   // device mask of the slots being finalised
+
+  int create(mdwf_ctx* c, Cfg* cf, int slots, const mdwf_solver_opts& opts, double tl, cudaStream_t s,
+             const std::string& prefix) {
+    mdwf_ctx* ctx = c;
+    this->ctx = c;
+    cfg = cf;
+    N = slots;
+    o = opts;
+    tol = tl;
+    st = s;
+    masses.assign(N, cf->act.mf);
+    used.assign(N, 0);
+    nupd.assign(N, 0);
+    tags.assign(N, 0);
+    outs.assign(N, nullptr);
+    b2.assign(N, 0.0);
+    t0.resize(N);
+    sv.wsp = prefix;
+    int rc = sv.init(c, cf, masses, o.nsb, o.profile != 0, o, s);
+    if (rc) return rc;
+    sv.sc.delta2 = BatchSolver<S>::kFP64 ? 0.0 : o.delta * o.delta;
+    sv.sc.tau2 = BatchSolver<S>::kFP64 ? 0.0 : 1e-10;
+    cudaError_t e = cudaSuccess;
+    fmask = (int*)ws_get(c, prefix + "fmask", sizeof(int) * N, &e);
+    CK(e);
+    CK(cudaStreamSynchronize(s));
+    return MDWF_OK;
+  }
+
+  int occupied() const override {
+    int k = 0;
+    for (int u : used) k += u;
+    return k;
+  }
+
+  int set_mask(int* dev, const std::vector<int>& h) {
+    CK(cudaMemcpyAsync(dev, h.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
+    return MDWF_OK;
+  }
+
+  int submit(const double* src, double mass, double* x, long long tag, int* slot) override {
+    int r = -1;
+    for (int i = 0; i < N; i++)
+      if (!used[i]) { r = i; break; }
+    if (r < 0) return fail(ctx, MDWF_ERR_FULL, "session has no free slot");
+    const Geom& g = ctx->g;
+    const int L5 = cfg->act.L5;
+    masses[r] = mass;
+    const float m32 = (float)mass;
+    CK(cudaMemcpyAsync(sv.mass64 + r, &mass, sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(sv.mass32 + r, &m32, sizeof(float), cudaMemcpyHostToDevice, st));
+    std::vector<int> um(N, 0);
+    um[r] = 1;
+    if (int rc = set_mask(sv.umask_d, um)) return rc;
+    // fresh per-slot state
+    const int zi = 0;
+    const double zd = 0.0;
+    int* ia[] = {sv.sc.active, sv.sc.flags, sv.sc.iters};
+    for (int* a : ia) CK(cudaMemcpyAsync(a + r, &zi, sizeof(int), cudaMemcpyHostToDevice, st));
+    double* da[] = {sv.sc.gamma, sv.sc.gamma_prev, sv.sc.alpha, sv.sc.beta, sv.sc.rho2, sv.sc.rho2_max, sv.sc.qq,
+                    sv.sc.rr, sv.sc.tmp, sv.sc.bhat2};
+    for (double* a : da)
+      CK(cudaMemcpyAsync(a + r, &zd, sizeof(double), cudaMemcpyHostToDevice, st));
+    const int* m = sv.umask_d;
+    CK(zero_masked<double>(sv.x_acc.v, nullptr, sv.tl_blas, g.Vh, L5, N, m, st));
+    CK(zero_masked<double>(sv.x_hi.v, nullptr, sv.tl_blas, g.Vh, L5, N, m, st));
+    CK(zero_masked<typename BatchSolver<S>::SX>(sv.xlo.v, nullptr, sv.tl_blas, g.Vh, L5, N, m, st));
+    CK(zero_masked<S>(sv.p.v, sv.p.n, sv.tl_blas, g.Vh, L5, N, m, st));
+    CK(pack_rhs<double>(src, sv.b_e.v, nullptr, g, L5, N, 0, r, st));
+    CK(pack_rhs<double>(src, sv.b_o.v, nullptr, g, L5, N, 1, r, st));
+    std::vector<double> be(N), bo(N);
+    CK(sv.norms(sv.b_e, m, sv.sc.tmp));
+    CK(cudaMemcpyAsync(be.data(), sv.sc.tmp, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
+    CK(sv.norms(sv.b_o, m, sv.sc.tmp));
+    CK(cudaMemcpyAsync(bo.data(), sv.sc.tmp, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    b2[r] = be[r] + bo[r];
+    if (!std::isfinite(b2[r])) return fail(ctx, MDWF_ERR_NONFINITE, "source has NaN/Inf");
+    const double stop2 = 0.25 * tol * tol * b2[r];
+    CK(cudaMemcpyAsync(sv.sc.stop2 + r, &stop2, sizeof(double), cudaMemcpyHostToDevice, st));
+    // bhat_e = b_e + 1/2 H_eo B A^-1 b_o on this slot
+    {
+      F<double> none;
+      Op<double, double> loc;
+      loc.g = g; loc.L5 = L5; loc.N = N; loc.anti = cfg->anti; loc.U = cfg->U64; loc.st = st;
+      loc.tl = tiling_for<double>(g, L5, N, sv.op64.tl.nsb, true);
+      Tables tab;
+      tab.build(cfg->act, masses);
+      DevTables<double> M;
+      CK(M.upload(tab, st));
+      CK(loc.run(false, 1, 0, sv.b_o, none, M[MK_BAinv], none, nullptr, 0.0, sv.t64, m, nullptr));
+      CK(sv.op64.run(E_RAW, 0, 0, sv.t64, none, sv.b_e, 0.0, 0.5, sv.bhat, m, nullptr));
+    }
+    const int one = 1;
+    CK(cudaMemcpyAsync(sv.sc.active + r, &one, sizeof(int), cudaMemcpyHostToDevice, st));
+    if (b2[r] > 0.0) {
+      CK(sv.reref(m, true));
+    } else {
+      const int done = FLAG_DONE;
+      CK(cudaMemcpyAsync(sv.sc.flags + r, &done, sizeof(int), cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(sv.sc.active + r, &zi, sizeof(int), cudaMemcpyHostToDevice, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    used[r] = 1;
+    nupd[r] = 1;
+    tags[r] = tag;
+    outs[r] = x;
+    t0[r] = std::chrono::steady_clock::now();
+    if (slot) *slot = r;
+    return MDWF_OK;
+  }
+
+  int launch(int iters) override {
+    if (occupied() == 0) return MDWF_OK;
+    return sv.run_chunk(iters > 0 ? iters : (o.chunk > 0 ? o.chunk : 16), o.use_graph != 0);
+  }
+
+  int poll(int max_done, long long* out_tags, mdwf_solve_stats* stats, int* n_done) override {
+    *n_done = 0;
+    if (occupied() == 0) return MDWF_OK;
+    const Geom& g = ctx->g;
+    const int L5 = cfg->act.L5;
+    std::vector<int> flags(N), iters(N), um(N);
+    auto read = [&]() -> int {
+      int herr = 0;
+      CK(cudaMemcpyAsync(flags.data(), sv.sc.flags, sizeof(int) * N, cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(iters.data(), sv.sc.iters, sizeof(int) * N, cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(&herr, sv.errw, sizeof(int), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      if (herr) return fail(ctx, MDWF_ERR_TIMEOUT, "a bounded device wait ran out");
+      return MDWF_OK;
+    };
+    if (int rc = read()) return rc;
+    CK(sv.collect(o.use_graph != 0));
+    bool any = false;
+    for (int i = 0; i < N; i++) {
+      um[i] = (used[i] && !(flags[i] & FLAG_DONE) && (flags[i] & (FLAG_INNER_DONE | FLAG_UPDATE))) ? 1 : 0;
+      any = any || um[i];
+    }
+    if (any) {
+      if (int rc = set_mask(sv.umask_d, um)) return rc;
+      if (BatchSolver<S>::kFP64) CK(sv.reref(sv.umask_d, false));
+      else CK(sv.update32(sv.umask_d));
+      if (int rc = read()) return rc;
+      CK(sv.collect(false));
+      for (int i = 0; i < N; i++) if (um[i]) nupd[i]++;
+    }
+    any = false;
+    for (int i = 0; i < N; i++) {
+      um[i] = (used[i] && !(flags[i] & FLAG_DONE) && (flags[i] & FLAG_REREF)) ? 1 : 0;
+      any = any || um[i];
+    }
+    if (any) {
+      if (int rc = set_mask(sv.umask_d, um)) return rc;
+      CK(sv.reref(sv.umask_d, false));
+      if (int rc = read()) return rc;
+      CK(sv.collect(false));
+      for (int i = 0; i < N; i++) if (um[i]) nupd[i]++;
+    }
+    // slots that finished (converged or out of iterations), up to max_done
+    std::vector<int> fin(N, 0);
+    int nf = 0;
+    for (int i = 0; i < N && nf < max_done; i++)
+      if (used[i] && ((flags[i] & FLAG_DONE) || iters[i] >= o.max_iter)) { fin[i] = 1; nf++; }
+    if (nf == 0) return MDWF_OK;
+    if (int rc = set_mask(fmask, fin)) return rc;
+    const int zi = 0;
+    for (int i = 0; i < N; i++)
+      if (fin[i]) CK(cudaMemcpyAsync(sv.sc.active + i, &zi, sizeof(int), cudaMemcpyHostToDevice, st));
+    F<double> none;
+    CK(accum_xhi<typename BatchSolver<S>::SX>(sv.x_hi.v, sv.xlo.v, sv.tl_blas, g.Vh, L5, N, fmask, st));
+    CK(accum_xhi<double>(sv.x_acc.v, sv.x_hi.v, sv.tl_blas, g.Vh, L5, N, fmask, st));
+    CK(bop<double>(sv.x_acc.v, nullptr, sv.u64.v, nullptr, sv.op64.f, sv.tl_blas, g.Vh, L5, N, fmask, st));
+    CK(sv.op64.run(E_AINV_SAME, 1, 0, sv.u64, sv.b_o, none, 0.0, 0.5, sv.x_o, fmask, nullptr));
+    CK(bop<double>(sv.x_o.v, nullptr, sv.t64.v, nullptr, sv.op64.f, sv.tl_blas, g.Vh, L5, N, fmask, st));
+    CK(sv.op64.run(E_A_SAME, 0, 0, sv.t64, sv.x_acc, sv.b_e, -1.0, 0.5, sv.rho64, fmask, nullptr));
+    std::vector<double> re(N), ro(N);
+    CK(sv.norms(sv.rho64, fmask, sv.sc.tmp));
+    CK(cudaMemcpyAsync(re.data(), sv.sc.tmp, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
+    CK(sv.op64.run(E_A_SAME, 1, 0, sv.u64, sv.x_o, sv.b_o, -1.0, 0.5, sv.rho64, fmask, nullptr));
+    CK(sv.norms(sv.rho64, fmask, sv.sc.tmp));
+    CK(cudaMemcpyAsync(ro.data(), sv.sc.tmp, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
+    for (int i = 0; i < N; i++) {
+      if (!fin[i]) continue;
+      CK(unpack_rhs<double>(sv.x_acc.v, nullptr, outs[i], g, L5, N, 0, i, st));
+      CK(unpack_rhs<double>(sv.x_o.v, nullptr, outs[i], g, L5, N, 1, i, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    auto now = std::chrono::steady_clock::now();
+    int k = 0;
+    for (int i = 0; i < N; i++) {
+      if (!fin[i]) continue;
+      const double rel = b2[i] > 0 ? std::sqrt((re[i] + ro[i]) / b2[i]) : 0.0;
+      if (out_tags) out_tags[k] = tags[i];
+      if (stats) {
+        std::memset(&stats[k], 0, sizeof(stats[k]));
+        stats[k].iters = iters[i];
+        stats[k].reliable_updates = nupd[i];
+        stats[k].converged = rel <= tol ? 1 : 0;
+        stats[k].rel_true_resid = rel;
+        stats[k].time_s = std::chrono::duration<double>(now - t0[i]).count();
+        stats[k].hop_units = (long long)g.Vh * L5 * N;
+      }
+      used[i] = 0;
+      const int zf = 0;
+      CK(cudaMemcpyAsync(sv.sc.flags + i, &zf, sizeof(int), cudaMemcpyHostToDevice, st));
+      k++;
+    }
+    CK(cudaStreamSynchronize(st));
+    *n_done = k;
+    return MDWF_OK;
+  }
+};
+
+void ws_release_prefix(mdwf_ctx* ctx, const std::string& prefix) {
+  for (auto it = ctx->ws.begin(); it != ctx->ws.end();) {
+    if (it->first.compare(0, prefix.size(), prefix) == 0) {
+      if (it->second.first) cudaFree(it->second.first);
+      it = ctx->ws.erase(it);
+    } else {
+      ++it;
+    }
   }
 }
 
@@ -1431,6 +1700,111 @@ int mdwf_apply_schur_batch_dev(mdwf_ctx* ctx, int cfg_id, int n, const double* c
     case MDWF_PREC_BF16: return schur_batch_impl<__nv_bfloat16>(ctx, cfg, n, in, out, m, dagger, flags, st);
     default: return fail(ctx, MDWF_ERR_ARG, "apply_schur_batch_dev: unknown precision");
   }
+}
+
+// --- sessions ---------------------------------------------------------------
+long long mdwf_session_bytes(mdwf_ctx* ctx, int cfg_id, int slots, int precision) {
+  if (!ctx) return -1;
+  auto it = ctx->cfgs.find(cfg_id);
+  if (it == ctx->cfgs.end() || !it->second.act.set || slots < 1) return -1;
+  const double units = (double)ctx->g.Vh * it->second.act.L5 * slots;
+  const double s = precision == MDWF_PREC_DOUBLE ? 192 : precision == MDWF_PREC_SINGLE ? 96
+                 : precision == MDWF_PREC_HALF ? 52 : 48;
+  const double x = precision == MDWF_PREC_DOUBLE ? 192 : 96;
+  const double f32 = precision == MDWF_PREC_DOUBLE ? 0 : 4 * 96;
+  // nine FP64 fields, the FP32 update fields, six inner fields, x_lo, partial sums
+  return (long long)(units * (9 * 192 + f32 + 6 * s + x) + (double)ctx->g.Vh * slots * 8 + 4096.0 * slots);
+}
+
+int mdwf_session_create(mdwf_ctx* ctx, int cfg_id, int slots, const mdwf_solver_opts* opts, double tol, void* stream,
+                        mdwf_session** out) {
+  if (!ctx || !out) return MDWF_ERR_ARG;
+  Cfg* cfg;
+  int rc = check_cfg(ctx, cfg_id, &cfg);
+  if (rc) return rc;
+  if (slots < 1 || slots > 1024 || !(tol > 0)) return fail(ctx, MDWF_ERR_ARG, "session_create: bad slots or tol");
+  mdwf_solver_opts o;
+  mdwf_default_opts(&o);
+  if (opts) o = *opts;
+  CK(cudaSetDevice(ctx->device));
+  mdwf_session* sess = new mdwf_session();
+  sess->ctx = ctx;
+  sess->prefix = "session" + std::to_string(ctx->next_session++) + ".";
+  sess->stream = pick_stream(ctx, stream);
+  switch (o.precision) {
+    case MDWF_PREC_DOUBLE: { auto* p = new SessionImpl<double>(); sess->impl = p; rc = p->create(ctx, cfg, slots, o, tol, sess->stream, sess->prefix); break; }
+    case MDWF_PREC_SINGLE: { auto* p = new SessionImpl<float>(); sess->impl = p; rc = p->create(ctx, cfg, slots, o, tol, sess->stream, sess->prefix); break; }
+    case MDWF_PREC_HALF: { auto* p = new SessionImpl<__half>(); sess->impl = p; rc = p->create(ctx, cfg, slots, o, tol, sess->stream, sess->prefix); break; }
+    case MDWF_PREC_BF16: { auto* p = new SessionImpl<__nv_bfloat16>(); sess->impl = p; rc = p->create(ctx, cfg, slots, o, tol, sess->stream, sess->prefix); break; }
+    default: rc = fail(ctx, MDWF_ERR_ARG, "session_create: unknown precision");
+  }
+  if (rc) {
+    delete sess->impl;
+    ws_release_prefix(ctx, sess->prefix);
+    delete sess;
+    return rc;
+  }
+  *out = sess;
+  return MDWF_OK;
+}
+
+int mdwf_session_destroy(mdwf_session* s) {
+  if (!s) return MDWF_OK;
+  cudaSetDevice(s->ctx->device);
+  cudaStreamSynchronize(s->stream);
+  delete s->impl;
+  ws_release_prefix(s->ctx, s->prefix);
+  delete s;
+  return MDWF_OK;
+}
+
+int mdwf_session_submit(mdwf_session* s, const double* src5d, double mass, double* x5d, long long tag, int* slot) {
+  if (!s) return MDWF_ERR_ARG;
+  mdwf_ctx* ctx = s->ctx;
+  if (!src5d || !x5d || !std::isfinite(mass)) return fail(ctx, MDWF_ERR_ARG, "session_submit: bad source, solution or mass");
+  CK(cudaSetDevice(ctx->device));
+  return s->impl->submit(src5d, mass, x5d, tag, slot);
+}
+
+int mdwf_session_launch(mdwf_session* s, int iters) {
+  if (!s) return MDWF_ERR_ARG;
+  mdwf_ctx* ctx = s->ctx;
+  CK(cudaSetDevice(ctx->device));
+  return s->impl->launch(iters);
+}
+
+int mdwf_session_poll(mdwf_session* s, int max_done, long long* tags, mdwf_solve_stats* stats, int* n_done) {
+  if (!s || !n_done || max_done < 0) return MDWF_ERR_ARG;
+  mdwf_ctx* ctx = s->ctx;
+  CK(cudaSetDevice(ctx->device));
+  return s->impl->poll(max_done, tags, stats, n_done);
+}
+
+int mdwf_session_occupied(const mdwf_session* s) { return s ? s->impl->occupied() : -1; }
+
+int mdwf_make_source_dev(mdwf_ctx* ctx, int cfg_id, const double* eta4d, double* src5d, void* stream) {
+  if (!ctx) return MDWF_ERR_ARG;
+  Cfg* cfg;
+  int rc = check_cfg(ctx, cfg_id, &cfg);
+  if (rc) return rc;
+  if (!eta4d || !src5d) return fail(ctx, MDWF_ERR_ARG, "make_source_dev: null pointer");
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = pick_stream(ctx, stream);
+  const size_t n5 = (size_t)cfg->act.L5 * ctx->g.V * 24;
+  cudaError_t e = cudaSuccess;
+  double* w = (double*)ws_get(ctx, "make_source.walls", sizeof(double) * n5, &e);
+  CK(e);
+  CK(cudaMemsetAsync(w, 0, sizeof(double) * n5, st));
+  CK(walls(eta4d, w, ctx->g.V, cfg->act.L5, st));
+  return apply_dev(ctx, cfg, 3, 0, 0, w, src5d, st);
+}
+
+int mdwf_z2_source_dev(mdwf_ctx* ctx, unsigned long long seed, double* eta4d, void* stream) {
+  if (!ctx) return MDWF_ERR_ARG;
+  if (!eta4d) return fail(ctx, MDWF_ERR_ARG, "z2_source_dev: null pointer");
+  CK(cudaSetDevice(ctx->device));
+  CK(z2_source(seed, eta4d, ctx->g.V, pick_stream(ctx, stream)));
+  return MDWF_OK;
 }
 
 int mdwf_extract_prop4d(const double* x5d, const int dims[4], int L5, double* q4d) {

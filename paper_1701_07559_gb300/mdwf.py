@@ -30,6 +30,7 @@ MDWF_ERR_NOT_CONVERGED = -4
 MDWF_ERR_TIMEOUT = -5
 MDWF_ERR_CUDA = -6
 MDWF_ERR_STATE = -7
+MDWF_ERR_FULL = -8
 
 MDWF_PREC_DOUBLE = 0
 MDWF_PREC_SINGLE = 1
@@ -90,6 +91,16 @@ _sig = {
     'mdwf_apply_dslash_dev': (_I, [_P, _I, _P, _P, _I, _I, _P]),
     'mdwf_apply_mdwf_dev': (_I, [_P, _I, _P, _P, _I, _P]),
     'mdwf_extract_prop4d': (_I, [_P, ctypes.POINTER(_I), _I, _P]),
+    'mdwf_session_bytes': (ctypes.c_longlong, [_P, _I, _I, _I]),
+    'mdwf_session_create': (_I, [_P, _I, _I, ctypes.POINTER(mdwf_solver_opts), _D, _P, ctypes.POINTER(_P)]),
+    'mdwf_session_destroy': (_I, [_P]),
+    'mdwf_session_submit': (_I, [_P, _P, _D, _P, ctypes.c_longlong, ctypes.POINTER(_I)]),
+    'mdwf_session_launch': (_I, [_P, _I]),
+    'mdwf_session_poll': (_I, [_P, _I, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(mdwf_solve_stats),
+                               ctypes.POINTER(_I)]),
+    'mdwf_session_occupied': (_I, [_P]),
+    'mdwf_make_source_dev': (_I, [_P, _I, _P, _P, _P]),
+    'mdwf_z2_source_dev': (_I, [_P, ctypes.c_ulonglong, _P, _P]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(_lib, _name)
@@ -366,3 +377,83 @@ def mdwf_extract_prop4d(x5d, dims, L5):
     if rc != MDWF_OK:
         raise MdwfError(rc, 'mdwf_extract_prop4d: bad arguments')
     return q
+
+
+def mdwf_make_source_dev(ctx, cfg_id, eta, out, stream=None):
+    """5D domain-wall source from a 4D source, on torch CUDA tensors."""
+    d = ctx.dims
+    shape4 = (d[3], d[2], d[1], d[0], 4, 3)
+    sh = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+    _check(ctx, _lib.mdwf_make_source_dev(ctx.handle, int(cfg_id), _dev_ptr(eta, shape4),
+                                          _dev_ptr(out, _shape5(ctx, cfg_id)), sh))
+
+
+def mdwf_z2_source_dev(ctx, seed, eta, stream=None):
+    """Z2 noise 4D source (counter-based SplitMix64 of seed) into a torch CUDA tensor."""
+    d = ctx.dims
+    sh = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+    _check(ctx, _lib.mdwf_z2_source_dev(ctx.handle, ctypes.c_ulonglong(int(seed) & (2 ** 64 - 1)),
+                                        _dev_ptr(eta, (d[3], d[2], d[1], d[0], 4, 3)), sh))
+
+
+class Session:
+    """Opaque handle of an mdwf_session (continuous batching of solves on one config)."""
+
+    def __init__(self, ctx, cfg_id, handle, slots):
+        self.ctx, self.cfg_id, self.handle, self.slots = ctx, cfg_id, handle, slots
+        self.keep = {}      # tag -> output tensor, kept alive until the request completes
+
+
+def mdwf_session_bytes(ctx, cfg_id, slots, precision=MDWF_PREC_HALF):
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    return int(_lib.mdwf_session_bytes(ctx.handle, int(cfg_id), int(slots), int(precision)))
+
+
+def mdwf_session_create(ctx, cfg_id, slots, tol, opts=None, stream=None):
+    o = opts if opts is not None else mdwf_default_opts()
+    h = _P()
+    sh = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+    _check(ctx, _lib.mdwf_session_create(ctx.handle, int(cfg_id), int(slots), ctypes.byref(o), float(tol), sh,
+                                         ctypes.byref(h)))
+    return Session(ctx, cfg_id, h, int(slots))
+
+
+def mdwf_session_destroy(sess):
+    if sess is not None and sess.handle:
+        _lib.mdwf_session_destroy(sess.handle)
+        sess.handle = None
+        sess.keep.clear()
+
+
+def mdwf_session_submit(sess, src, mass, x, tag):
+    """Put a request (device source src, mass, device output x, integer tag) into a
+    free slot; returns the slot.  Raises MdwfError(MDWF_ERR_FULL) when none is free."""
+    shape = _shape5(sess.ctx, sess.cfg_id)
+    slot = _I(-1)
+    _check(sess.ctx, _lib.mdwf_session_submit(sess.handle, _dev_ptr(src, shape), float(mass), _dev_ptr(x, shape),
+                                              int(tag), ctypes.byref(slot)))
+    sess.keep[int(tag)] = x
+    return slot.value
+
+
+def mdwf_session_launch(sess, iters=0):
+    _check(sess.ctx, _lib.mdwf_session_launch(sess.handle, int(iters)))
+
+
+def mdwf_session_poll(sess, max_done=None):
+    """Returns [(tag, stats dict), ...] of the requests completed by this call."""
+    n = sess.slots if max_done is None else int(max_done)
+    tags = (ctypes.c_longlong * max(n, 1))()
+    st = (mdwf_solve_stats * max(n, 1))()
+    nd = _I(0)
+    _check(sess.ctx, _lib.mdwf_session_poll(sess.handle, n, tags, st, ctypes.byref(nd)))
+    out = []
+    for i in range(nd.value):
+        sess.keep.pop(int(tags[i]), None)
+        out.append((int(tags[i]), st[i].as_dict()))
+    return out
+
+
+def mdwf_session_occupied(sess):
+    return int(_lib.mdwf_session_occupied(sess.handle))

@@ -146,6 +146,29 @@ def z2_source_4d(dims, seed):
     return (2.0 * rng.integers(0, 2, size=(Lt, Lz, Ly, Lx, 4, 3)) - 1.0).astype(np.complex128)
 
 
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+
+
+def splitmix64(seed, n):
+    """First n outputs of SplitMix64 from state `seed` (Steele, Lea and Flood,
+    OOPSLA 2014): state += golden-ratio increment, output = mix(state)."""
+    with np.errstate(over='ignore'):
+        z = np.uint64(seed & (2 ** 64 - 1)) + np.arange(1, n + 1, dtype=np.uint64) * _GOLDEN
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        return z ^ (z >> np.uint64(31))
+
+
+def z2_source_4d_counter(dims, seed):
+    """Real Z2 noise (+-1) on every 4D site, spin and colour: element k in
+    [t, z, y, x, spin, colour] order takes its sign from the top bit of the k-th
+    SplitMix64 output of `seed` (counter based: any element is computable alone)."""
+    Lx, Ly, Lz, Lt = dims
+    z = splitmix64(seed, Lx * Ly * Lz * Lt * 12)
+    sign = 1.0 - 2.0 * (z >> np.uint64(63)).astype(np.float64)
+    return sign.reshape(Lt, Lz, Ly, Lx, 4, 3).astype(np.complex128)
+
+
 def point_source_4d(dims, spin, colour, site=(0, 0, 0, 0)):
     """Unit point source at site = (x, y, z, t)."""
     Lx, Ly, Lz, Lt = dims

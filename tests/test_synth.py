@@ -113,3 +113,26 @@ def test_flow_weak_field_is_heat_equation():
                  - np.roll(theta[..., mu], -1, axis=ax[nu]) - theta[..., nu])
             expect[..., mu] -= F - np.roll(F, 1, axis=ax[nu])
     assert np.abs(dtheta - expect).max() < 1e-3 * np.abs(expect).max()
+
+
+def test_splitmix64_reference_outputs():
+    """SplitMix64 (Steele, Lea and Flood 2014) against its published reference
+    outputs: state 0 and state 1234567 (the values quoted with the reference C
+    implementation and Java's SplittableRandom)."""
+    assert [int(v) for v in synth.splitmix64(0, 3)] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+    assert [int(v) for v in synth.splitmix64(1234567, 3)] == [6457827717110365317, 3203168211198807973,
+                                                              9817491932198370423]
+
+
+def test_z2_counter_source():
+    dims = (4, 2, 2, 6)
+    eta = synth.z2_source_4d_counter(dims, 77)
+    assert eta.shape == (6, 2, 2, 4, 4, 3)
+    assert np.all(eta.imag == 0) and np.all(np.abs(eta.real) == 1)
+    # element k from the k-th generator output alone
+    z = synth.splitmix64(77, eta.size)
+    k = 123
+    assert eta.ravel()[k].real == (-1.0 if int(z[k]) >> 63 else 1.0)
+    big = synth.z2_source_4d_counter((8, 8, 8, 8), 5)
+    assert abs(big.real.mean()) < 4.0 / np.sqrt(big.size)
+    assert not np.array_equal(big, synth.z2_source_4d_counter((8, 8, 8, 8), 6))
