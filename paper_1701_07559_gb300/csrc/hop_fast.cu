@@ -80,7 +80,7 @@ __device__ __forceinline__ void project(const T* p, T sg, T* h) {
 
 // fp16: project the packed (scaled) values with half2 arithmetic, then unpack and scale.
 template <int MU>
-__device__ __forceinline__ void project_half(const uint4 q[3], float s, float sg, float* h) {
+__device__ __forceinline__ void project_half(const uint4 q[3], float sg, float* h) {
   const __half2* w = reinterpret_cast<const __half2*>(q);   // w[4 * colour + spin] (colour-major storage)
   const __half2 pp = __floats2half2_rn(sg, sg);
   const __half2 mp = __floats2half2_rn(-sg, sg);             // times swapped z: sg * i * z
@@ -102,53 +102,56 @@ __device__ __forceinline__ void project_half(const uint4 q[3], float s, float sg
       h1 = __hfma2(p3, pp, p1);
     }
     const float2 f0 = __half22float2(h0), f1 = __half22float2(h1);
-    h[2 * c] = f0.x * s; h[2 * c + 1] = f0.y * s;
-    h[6 + 2 * c] = f1.x * s; h[6 + 2 * c + 1] = f1.y * s;
+    h[2 * c] = f0.x; h[2 * c + 1] = f0.y;
+    h[6 + 2 * c] = f1.x; h[6 + 2 * c + 1] = f1.y;
   }
 }
 
-// Load (global memory or shared memory) and project one neighbour spinor.
+// Load (global memory or shared memory) and project one neighbour spinor.  The
+// returned factor multiplies the projected spinor (the fp16 storage scale; 1 else)
+// and is applied in the reconstruction.
 template <int MU, typename S, typename T>
 struct Proj {
-  static __device__ __forceinline__ void global(const S* __restrict__ v, const float* __restrict__ nrm, long u, T sg,
-                                                T* h) {
+  static __device__ __forceinline__ T global(const S* __restrict__ v, const float* __restrict__ nrm, long u, T sg,
+                                             T* h) {
     T psi[24];
     load24<S, T>(v, nrm, u, psi);
     project<MU, T>(psi, sg, h);
+    return T(1);
   }
-  static __device__ __forceinline__ void shared(const S* sp, float nrm, T sg, T* h) {
+  static __device__ __forceinline__ T shared(const S* sp, float nrm, T sg, T* h) {
     T psi[24];
     load24_smem<S, T>(sp, psi);
-    if (StoreTraits<S>::kNorm) {
-#pragma unroll
-      for (int i = 0; i < 24; i++) psi[i] *= (T)nrm;
-    }
     project<MU, T>(psi, sg, h);
+    return StoreTraits<S>::kNorm ? (T)nrm : T(1);
   }
 };
 template <int MU>
 struct Proj<MU, __half, float> {
-  static __device__ __forceinline__ void global(const __half* __restrict__ v, const float* __restrict__ nrm, long u,
-                                                float sg, float* h) {
+  static __device__ __forceinline__ float global(const __half* __restrict__ v, const float* __restrict__ nrm, long u,
+                                                 float sg, float* h) {
     const uint4* p = reinterpret_cast<const uint4*>(v + 24 * u);
     uint4 q[3];
     q[0] = __ldg(p);
     q[1] = __ldg(p + 1);
     q[2] = __ldg(p + 2);
-    project_half<MU>(q, __ldg(nrm + u), sg, h);
+    project_half<MU>(q, sg, h);
+    return __ldg(nrm + u);
   }
-  static __device__ __forceinline__ void shared(const __half* sp, float nrm, float sg, float* h) {
+  static __device__ __forceinline__ float shared(const __half* sp, float nrm, float sg, float* h) {
     const uint4* p = reinterpret_cast<const uint4*>(sp);
     uint4 q[3];
     q[0] = p[0];
     q[1] = p[1];
     q[2] = p[2];
-    project_half<MU>(q, nrm, sg, h);
+    project_half<MU>(q, sg, h);
+    return nrm;
   }
 };
 
 template <int MU, typename T>
-__device__ __forceinline__ void reconstruct(const T* chi, T sg, T* acc) {
+__device__ __forceinline__ void reconstruct(const T* chi, T f, T fs, T* acc) {
+  // f: factor of the projected spinor (storage scale x boundary phase); fs = f sg
 #pragma unroll
   for (int c = 0; c < 3; c++) {
     const T* x0 = chi + 2 * c;
@@ -157,20 +160,20 @@ __device__ __forceinline__ void reconstruct(const T* chi, T sg, T* acc) {
     T* a1 = acc + 6 + 2 * c;
     T* a2 = acc + 12 + 2 * c;
     T* a3 = acc + 18 + 2 * c;
-    a0[0] += x0[0]; a0[1] += x0[1];
-    a1[0] += x1[0]; a1[1] += x1[1];
+    a0[0] += f * x0[0]; a0[1] += f * x0[1];
+    a1[0] += f * x1[0]; a1[1] += f * x1[1];
     if (MU == 0) {
-      a2[0] += sg * x1[1]; a2[1] -= sg * x1[0];
-      a3[0] += sg * x0[1]; a3[1] -= sg * x0[0];
+      a2[0] += fs * x1[1]; a2[1] -= fs * x1[0];
+      a3[0] += fs * x0[1]; a3[1] -= fs * x0[0];
     } else if (MU == 1) {
-      a2[0] += sg * x1[0]; a2[1] += sg * x1[1];
-      a3[0] -= sg * x0[0]; a3[1] -= sg * x0[1];
+      a2[0] += fs * x1[0]; a2[1] += fs * x1[1];
+      a3[0] -= fs * x0[0]; a3[1] -= fs * x0[1];
     } else if (MU == 2) {
-      a2[0] += sg * x0[1]; a2[1] -= sg * x0[0];
-      a3[0] -= sg * x1[1]; a3[1] += sg * x1[0];
+      a2[0] += fs * x0[1]; a2[1] -= fs * x0[0];
+      a3[0] -= fs * x1[1]; a3[1] += fs * x1[0];
     } else {
-      a2[0] += sg * x0[0]; a2[1] += sg * x0[1];
-      a3[0] += sg * x1[0]; a3[1] += sg * x1[1];
+      a2[0] += fs * x0[0]; a2[1] += fs * x0[1];
+      a3[0] += fs * x1[0]; a3[1] += fs * x1[1];
     }
   }
 }
@@ -212,12 +215,10 @@ __device__ __forceinline__ void hop_term(const FastArgs<S, T>& a, const Site& x,
   const int hn = nbr_half<MU, FWD>(a.g, x);
   const T sg = (a.dagger ? T(1) : T(-1)) * (FWD ? T(1) : T(-1));
   T hh[12], chi[12], l[18];
-  if (sp == nullptr) Proj<MU, S, T>::global(a.in, a.in_nrm, ((long)hn * a.L5 + s) * a.N + r, sg, hh);
-  else Proj<MU, S, T>::shared(sp, snrm, sg, hh);
-  if (MU == 3 && a.antiperiodic && (FWD ? x.c[3] == a.g.L[3] - 1 : x.c[3] == 0)) {
-#pragma unroll
-    for (int i = 0; i < 12; i++) hh[i] = -hh[i];
-  }
+  T f;
+  if (sp == nullptr) f = Proj<MU, S, T>::global(a.in, a.in_nrm, ((long)hn * a.L5 + s) * a.N + r, sg, hh);
+  else f = Proj<MU, S, T>::shared(sp, snrm, sg, hh);
+  if (MU == 3 && a.antiperiodic && (FWD ? x.c[3] == a.g.L[3] - 1 : x.c[3] == 0)) f = -f;
   if (FWD) {
     load_link<T>(a.U, ((long)a.out_par * a.g.Vh + h) * 4 + MU, l);
     su3_mul<T, false>(l, hh, chi);
@@ -227,7 +228,7 @@ __device__ __forceinline__ void hop_term(const FastArgs<S, T>& a, const Site& x,
     su3_mul<T, true>(l, hh, chi);
     su3_mul<T, true>(l, hh + 6, chi + 6);
   }
-  reconstruct<MU, T>(chi, sg, acc);
+  reconstruct<MU, T>(chi, f, f * sg, acc);
 }
 
 // A (dag = false) or A^+ (dag = true) of the stored field `same` at (h, s, r):
@@ -317,6 +318,53 @@ __device__ __forceinline__ void col_bop(Col<T> c, int L5, T b5, T c5, T m) {
   for (; k < L5; k++) { T v = c[k]; c[k] = b5 * v + c5 * prev; prev = v; }
 }
 
+// Register versions of the recursions for a column of compile-time length L
+// (same operations in the same order as col_ainv / col_bop).
+template <int L, typename T>
+__device__ __forceinline__ void ainv_regs(T* v, T inv_alpha, T kap, T m, T powL) {
+  T z = 0;
+#pragma unroll
+  for (int k = 0; k < L; k++) { z = v[k] * inv_alpha - kap * z; v[k] = z; }
+  const T yl = z / (T(1) + m * powL);
+  v[L - 1] = yl;
+  const T mk = -kap;
+  T w = m * yl * mk;
+#pragma unroll
+  for (int k = 0; k < L - 1; k++) { v[k] -= w; w *= mk; }
+}
+template <int L, typename T>
+__device__ __forceinline__ void bop_regs(T* v, T b5, T c5, T m) {
+  T prev = -m * v[L - 1];
+#pragma unroll
+  for (int k = 0; k < L; k++) { const T x = v[k]; v[k] = b5 * x + c5 * prev; prev = x; }
+}
+
+// The columns comp = s0, s0 + L, ... of one (site, slot): loaded into registers
+// along the recursion direction, transformed, stored back.
+template <int L, int EPI, typename T>
+__device__ __forceinline__ void cols_regs(T* base, int st, int s0, const Fifth<T>& f, T m) {
+  for (int comp = s0; comp < 24; comp += L) {
+    const bool upper = comp < 12;
+    const bool down = (EPI == E_AINVD_BD) ? !upper : upper;
+    T* p = base + comp + (down ? 0 : (L - 1) * st);
+    const int step = down ? st : -st;
+    T v[L];
+#pragma unroll
+    for (int k = 0; k < L; k++) v[k] = p[k * step];
+    if (EPI == E_BAINV) {
+      ainv_regs<L, T>(v, f.inv_alpha, f.kap, m, f.powL);
+      bop_regs<L, T>(v, f.b5, f.c5, m);
+    } else if (EPI == E_AINVD_BD) {
+      bop_regs<L, T>(v, f.b5, f.c5, m);
+      ainv_regs<L, T>(v, f.inv_alpha, f.kap, m, f.powL);
+    } else {
+      ainv_regs<L, T>(v, f.inv_alpha, f.kap, m, f.powL);
+    }
+#pragma unroll
+    for (int k = 0; k < L; k++) p[k * step] = v[k];
+  }
+}
+
 constexpr int kPadF = 25;
 
 // Thread coordinates of the (rt, L5, nsb) block.
@@ -346,31 +394,51 @@ __device__ __forceinline__ Thr thread_of(const FastArgs<S, T>& a, const Tiling& 
 // Epilogue shared by both hop variants: turns the hop sums acc into the output
 // of the selected fifth-dimension form, stores it and forms the norm partials.
 // sA: shared tile of (threads x kPadF) reals, also used for the partial sums.
-template <typename S, typename T, int EPI>
+// IN_SMEM: the hop sums, kappa included, are already in row tid of sA (acc unused).
+template <typename S, typename T, int EPI, bool IN_SMEM = false>
 __device__ __forceinline__ void epilogue(const FastArgs<S, T>& a, const Tiling& tl, const Thr& t, const T* acc,
                                          T* sA) {
   const int L5 = a.L5;
   const T m = t.valid ? a.f.mass[t.r] : T(0);
   T o[24];
   constexpr bool kCols = (EPI == E_BAINV || EPI == E_AINVD_BD || EPI == E_AINV_SAME);
+  if (IN_SMEM) __syncthreads();
   if (kCols || EPI == E_AD_SAME_BD) {
-    T v[24];
+    if (!IN_SMEM) {
+      T v[24];
 #pragma unroll
-    for (int i = 0; i < 24; i++) v[i] = a.kappa * acc[i];
-    if (EPI == E_AINV_SAME && t.act) {
-      T y[24];
-      load24<S, T>(a.same, a.same_nrm, t.u, y);
+      for (int i = 0; i < 24; i++) v[i] = a.kappa * acc[i];
+      if (EPI == E_AINV_SAME && t.act) {
+        T y[24];
+        load24<S, T>(a.same, a.same_nrm, t.u, y);
 #pragma unroll
-      for (int i = 0; i < 24; i++) v[i] += y[i];
+        for (int i = 0; i < 24; i++) v[i] += y[i];
+      }
+#pragma unroll
+      for (int i = 0; i < 24; i++) sA[t.tid * kPadF + i] = v[i];
+      __syncthreads();
+    } else if (EPI == E_AINV_SAME) {
+      if (t.act) {
+        T y[24];
+        load24<S, T>(a.same, a.same_nrm, t.u, y);
+#pragma unroll
+        for (int i = 0; i < 24; i++) sA[t.tid * kPadF + i] += y[i];
+      }
+      __syncthreads();
     }
-#pragma unroll
-    for (int i = 0; i < 24; i++) sA[t.tid * kPadF + i] = v[i];
-    __syncthreads();
     if (kCols) {
       // thread (r_l, s, site_l) runs the columns comp = s, s + L5, ... of (site_l, r_l)
       if (t.act) {
         const int st = tl.rt * kPadF;
         T* base = sA + (size_t)(t.site_l * L5 * tl.rt + t.r_l) * kPadF;
+        switch (L5) {
+          case 4: cols_regs<4, EPI, T>(base, st, t.s, a.f, m); break;
+          case 6: cols_regs<6, EPI, T>(base, st, t.s, a.f, m); break;
+          case 8: cols_regs<8, EPI, T>(base, st, t.s, a.f, m); break;
+          case 10: cols_regs<10, EPI, T>(base, st, t.s, a.f, m); break;
+          case 12: cols_regs<12, EPI, T>(base, st, t.s, a.f, m); break;
+          case 16: cols_regs<16, EPI, T>(base, st, t.s, a.f, m); break;
+          default:
         for (int comp = t.s; comp < 24; comp += L5) {
           const bool upper = comp < 12;
           if (EPI == E_BAINV) {
@@ -385,6 +453,7 @@ __device__ __forceinline__ void epilogue(const FastArgs<S, T>& a, const Tiling& 
             Col<T> c = make_col<T>(base + comp, st, L5, upper);
             col_ainv<T>(c, L5, a.f.inv_alpha, a.f.kap, m, a.f.powL);
           }
+        }
         }
       }
       __syncthreads();
@@ -405,6 +474,9 @@ __device__ __forceinline__ void epilogue(const FastArgs<S, T>& a, const Tiling& 
 #pragma unroll
       for (int i = 12; i < 24; i++) o[i] = a.f.b5 * me[i] + cl * nd[i];
     }
+  } else if (IN_SMEM) {
+#pragma unroll
+    for (int i = 0; i < 24; i++) o[i] = sA[t.tid * kPadF + i];
   } else {
 #pragma unroll
     for (int i = 0; i < 24; i++) o[i] = a.kappa * acc[i];
@@ -639,31 +711,27 @@ int max_threads_one() {
 }
 
 // ---------------------------------------------------------------------------
-// Tensor-core variant for fp16 storage.  For one direction mu, the colour
-// multiply of all (slice, RHS) units of a site by the same link is a small
-// dense product.  A warp takes a tile of 16 units of one site and, per mu,
-// four mma.sync.m16n8k16 (fp16 operands, FP32 accumulation):
-//   A (16 x 16): row i = unit i of the tile; columns 0..7 = (re, im) of the
-//                three colours (+ padding) of the forward term's projected
-//                spin component, columns 8..15 the backward term's;
-//   B (16 x 8):  rows 0..7 the real form of U_mu(x) (forward), rows 8..15 of
-//                U_mu(x - mu)^+ (backward): B[2b][2a] = Re W_ab, B[2b+1][2a] = -Im W_ab,
-//                B[2b][2a+1] = Im W_ab, B[2b+1][2a+1] = Re W_ab;
-//   C (16 x 8):  (re, im) of colour a of sum_d W_d h_d, accumulated over mu.
-// The two spin components k of the projected spinor h and of the rotated
-// spinor g = sg e_mu^+ h (which feeds the lower spins) use one mma each:
-// up_k += h_k B, lo_k += g_k B.  Every unit has its own fp16 scale per
-// neighbour; they are divided by the unit's largest neighbour scale and folded
-// into A (so A stays within fp16 range), and the FP32 result is multiplied by
-// that largest scale at the end.  Lane (g, c), c = lane % 4, loads colour c of
-// units g and g + 8 (one 16-byte word each); lanes with c = 3 carry zeros.
+// Tensor-core variant for fp16 storage.  For one direction, the colour
+// multiply of all (slice, RHS) units of a site by the same link W (U_mu(x)
+// forward, U_mu(x - mu)^+ backward) is a product with a shared 3 x 3 matrix.
+// A warp takes a tile of 8 units of one site and, per direction, one
+// mma.sync.m16n8k8 (fp16 operands, FP32 accumulation):
+//   A (16 x 8): row g = projected half spinor h_0 of unit g, row g + 8 = h_1;
+//               columns (re, im) of the three colours (+ one zero pair);
+//   B (8 x 8):  the real form of W: B[2b][2a] = Re W_ab, B[2b+1][2a] = -Im W_ab,
+//               B[2b][2a+1] = Im W_ab, B[2b+1][2a+1] = Re W_ab (zero for a, b = 3);
+//   D (16 x 8): (re, im) of colour a of W h_0 (rows g) and W h_1 (rows g + 8).
+// Lane (g, c), c = lane % 4, loads colour c of unit g (one 16-byte word of the
+// colour-major fp16 spinor), holds exactly the A entries it needs and receives
+// colour c of both products, so the spin reconstruction, with the unit's scale
+// and kappa applied in FP32, stays in the lane.  Lanes with c = 3 carry zeros.
+// B fragments come precomputed per link and lane (one coalesced word each).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void mma_m16n8k16(const uint32_t a[4], uint32_t b0, uint32_t b1, float d[4]) {
+__device__ __forceinline__ void mma_m16n8k8(uint32_t a0, uint32_t a1, uint32_t b0, float d[4]) {
   asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};"
+      "mma.sync.aligned.m16n8k8.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%0,%1,%2,%3};"
       : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+      : "r"(a0), "r"(a1), "r"(b0));
 }
 
 __device__ __forceinline__ uint32_t h2u(__half2 h) { return *reinterpret_cast<uint32_t*>(&h); }
@@ -671,169 +739,409 @@ __device__ __forceinline__ __half2 u2h(uint32_t u) { return *reinterpret_cast<__
 __device__ __forceinline__ uint32_t swap_hl(uint32_t x) { return __byte_perm(x, 0, 0x1032); }
 constexpr uint32_t kNegHi = 0x80000000u, kNegLo = 0x00008000u;
 
-// Projected (h0, h1) and rotated (g0, g1) half spinors of colour c of one unit,
-// scaled by r (fp16 pair), from the 16-byte word q = spins 0..3 of that colour.
+// Projection h = psi_up + sg e_mu psi_lo of one colour (p0..p3 = spins 0..3 as
+// (re, im) fp16 pairs); e_x = i sigma_x, e_y = -i sigma_y, e_z = i sigma_z, e_t = 1.
+// i z = swap(z) with the low half negated.
 template <int MU>
-__device__ __forceinline__ void mma_project(uint4 q, __half2 r, bool neg_sg, uint32_t& h0, uint32_t& h1, uint32_t& g0,
-                                            uint32_t& g1) {
-  const uint32_t sgn = neg_sg ? (kNegHi | kNegLo) : 0u;   // multiply by sg = -1
-  const __half2 p0 = u2h(q.x), p1 = u2h(q.y), p2 = u2h(q.z), p3 = u2h(q.w);
-  __half2 a0, a1;
-  // h = psi_up + sg e_mu psi_lo ; e_x = i sigma_x, e_y = -i sigma_y, e_z = i sigma_z, e_t = 1
+__device__ __forceinline__ void mma_project(uint4 q, bool neg_sg, uint32_t& h0, uint32_t& h1) {
+  const uint32_t sgn = neg_sg ? (kNegHi | kNegLo) : 0u;
+  const __half2 p0 = u2h(q.x), p1 = u2h(q.y);
   if (MU == 0) {        // (i p3, i p2)
-    a0 = __hadd2(p0, u2h(swap_hl(h2u(p3)) ^ kNegLo ^ sgn));
-    a1 = __hadd2(p1, u2h(swap_hl(h2u(p2)) ^ kNegLo ^ sgn));
+    h0 = h2u(__hadd2(p0, u2h(swap_hl(q.w) ^ kNegLo ^ sgn)));
+    h1 = h2u(__hadd2(p1, u2h(swap_hl(q.z) ^ kNegLo ^ sgn)));
   } else if (MU == 1) { // (-p3, p2)
-    a0 = __hadd2(p0, u2h(h2u(p3) ^ (kNegHi | kNegLo) ^ sgn));
-    a1 = __hadd2(p1, u2h(h2u(p2) ^ sgn));
+    h0 = h2u(__hadd2(p0, u2h(q.w ^ (kNegHi | kNegLo) ^ sgn)));
+    h1 = h2u(__hadd2(p1, u2h(q.z ^ sgn)));
   } else if (MU == 2) { // (i p2, -i p3)
-    a0 = __hadd2(p0, u2h(swap_hl(h2u(p2)) ^ kNegLo ^ sgn));
-    a1 = __hadd2(p1, u2h(swap_hl(h2u(p3)) ^ kNegHi ^ sgn));
+    h0 = h2u(__hadd2(p0, u2h(swap_hl(q.z) ^ kNegLo ^ sgn)));
+    h1 = h2u(__hadd2(p1, u2h(swap_hl(q.w) ^ kNegHi ^ sgn)));
   } else {              // (p2, p3)
-    a0 = __hadd2(p0, u2h(h2u(p2) ^ sgn));
-    a1 = __hadd2(p1, u2h(h2u(p3) ^ sgn));
-  }
-  h0 = h2u(__hmul2(a0, r));
-  h1 = h2u(__hmul2(a1, r));
-  // g = sg e_mu^+ h ;  -i z = swap(z) with the high half negated, i z = swap(z) with the low half negated
-  if (MU == 0) {        // (-i h1, -i h0)
-    g0 = swap_hl(h1) ^ kNegHi ^ sgn;
-    g1 = swap_hl(h0) ^ kNegHi ^ sgn;
-  } else if (MU == 1) { // (h1, -h0)
-    g0 = h1 ^ sgn;
-    g1 = h0 ^ (kNegHi | kNegLo) ^ sgn;
-  } else if (MU == 2) { // (-i h0, i h1)
-    g0 = swap_hl(h0) ^ kNegHi ^ sgn;
-    g1 = swap_hl(h1) ^ kNegLo ^ sgn;
-  } else {              // (h0, h1)
-    g0 = h0 ^ sgn;
-    g1 = h1 ^ sgn;
+    h0 = h2u(__hadd2(p0, u2h(q.z ^ sgn)));
+    h1 = h2u(__hadd2(p1, u2h(q.w ^ sgn)));
   }
 }
 
-// B fragment of lane (g, c): rows 2c, 2c+1, column g (colour a = g / 2, part g % 2)
-// of the real form of W = U (forward) or U^+ (backward).
-__device__ __forceinline__ uint32_t mma_link(const __half2* __restrict__ U16, long link, int g, int c, bool fwd) {
-  const int ca = g >> 1;
-  if (c == 3 || ca == 3) return 0u;
-  // W_ab = U_ab (forward) or conj(U_ba) (backward), a = ca, b = c
-  const uint32_t e = h2u(__ldg(U16 + link * 9 + (fwd ? ca * 3 + c : c * 3 + ca)));
-  if (g & 1) return fwd ? swap_hl(e) : (swap_hl(e) ^ kNegLo);    // (Im W, Re W)
-  return fwd ? (e ^ kNegHi) : e;                                   // (Re W, -Im W)
+// acc[2 spin + (re, im)] of one colour += the reconstructed term: spins 0, 1 get
+// f x_k, spins 2, 3 get f sg e_mu^+ (x_0, x_1), with x_0 = (d0, d1), x_1 = (d2, d3).
+template <int MU>
+__device__ __forceinline__ void mma_reconstruct(const float d[4], float f, float fs, float* acc) {
+  acc[0] += f * d[0]; acc[1] += f * d[1];
+  acc[2] += f * d[2]; acc[3] += f * d[3];
+  if (MU == 0) {        // (-i x1, -i x0)
+    acc[4] += fs * d[3]; acc[5] -= fs * d[2];
+    acc[6] += fs * d[1]; acc[7] -= fs * d[0];
+  } else if (MU == 1) { // (x1, -x0)
+    acc[4] += fs * d[2]; acc[5] += fs * d[3];
+    acc[6] -= fs * d[0]; acc[7] -= fs * d[1];
+  } else if (MU == 2) { // (-i x0, i x1)
+    acc[4] += fs * d[1]; acc[5] -= fs * d[0];
+    acc[6] -= fs * d[3]; acc[7] += fs * d[2];
+  } else {              // (x0, x1)
+    acc[4] += fs * d[0]; acc[5] += fs * d[1];
+    acc[6] += fs * d[2]; acc[7] += fs * d[3];
+  }
 }
+
+// One of the eight terms for the tile's 8 units (lane: unit g, colour c).
+// One of the eight terms for the tile's 8 units (lane: unit g, colour c), from
+// the loaded colour word q, the neighbour's scale sc and the link fragment b.
+template <int MU, bool FWD>
+__device__ __forceinline__ void mma_term(uint4 q, float sc, uint32_t b, bool dag, float kb, float* acc) {
+  // sg = -1 for the forward term of H, +1 backward; exchanged for H^+
+  const bool neg_sg = FWD ? !dag : dag;
+  uint32_t h0, h1;
+  mma_project<MU>(q, neg_sg, h0, h1);
+  float d[4] = {0.f, 0.f, 0.f, 0.f};
+  mma_m16n8k8(h0, h1, b, d);
+  const float f = sc * kb;
+  mma_reconstruct<MU>(d, f, neg_sg ? -f : f, acc);
+}
+
+// Shared-memory tables of a block: neighbour half-site index and kappa x
+// time-boundary phase per (site, direction); the in-site memory offset of each
+// block-local unit (-1: slot out of range or inactive); (site, first unit) of each tile.
+struct MmaTables {
+  int* nb;
+  float* kb;
+  int* off;
+  int* tile;
+};
 
 template <int EPI>
-__global__ void hop_mma_kernel(FastArgs<__half, float> a, Tiling tl) {
+__global__ void hop_mma_kernel(FastArgs<__half, float> a, Tiling tl, const uint32_t* __restrict__ frag) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* sA = reinterpret_cast<float*>(smem_raw);
   const Thr t = thread_of(a, tl);
-  const int nthr = blockDim.x * blockDim.y * blockDim.z;
-  Site* sSite = reinterpret_cast<Site*>(smem_raw + (size_t)nthr * kPadF * sizeof(float));
-  const int upb = a.L5 * a.N;                      // units per site (rt == N)
-  const int lane = t.tid & 31, warp = t.tid >> 5, nwarp = nthr >> 5;
-  const int g = lane >> 2, c = lane & 3;
+  const int nthr = tl.threads;
+  const int upb = a.L5 * tl.rt;                   // units of one site in this block
+  const int tps = (upb + 7) >> 3;                 // 8-unit tiles per site
+  const int ntile = tl.nsb * tps;
+  size_t base = (size_t)nthr * kPadF * sizeof(float);
+  if (base < (size_t)nthr * sizeof(double)) base = (size_t)nthr * sizeof(double);
+  MmaTables tb;
+  tb.nb = reinterpret_cast<int*>(smem_raw + base);
+  tb.kb = reinterpret_cast<float*>(tb.nb + 8 * tl.nsb);
+  tb.off = reinterpret_cast<int*>(tb.kb + 8 * tl.nsb);
+  tb.tile = tb.off + upb;
   const long h0 = (long)blockIdx.x * tl.nsb;
-  if (t.tid < tl.nsb && h0 + t.tid < a.g.Vh) sSite[t.tid] = make_site(a.g, a.out_par, h0 + t.tid);
-  __syncthreads();
-  const uint4* in4 = reinterpret_cast<const uint4*>(a.in);
-  const int ntile = (tl.nsb * upb) >> 4;
-  const bool dag = a.dagger != 0;
-  for (int tile = warp; tile < ntile; tile += nwarp) {
-    const int j = (tile << 4) / upb;
+  for (int k = t.tid; k < 8 * tl.nsb; k += nthr) {
+    const int j = k >> 3, d = k & 7;
     const long h = h0 + j;
-    if (h >= a.g.Vh) continue;                     // the whole warp skips together
-    const Site x = sSite[j];
-    const int lu0 = (tile << 4) - j * upb + g, lu1 = lu0 + 8;
-    int hn[8];
-    hn[0] = nbr_half<0, true>(a.g, x); hn[1] = nbr_half<0, false>(a.g, x);
-    hn[2] = nbr_half<1, true>(a.g, x); hn[3] = nbr_half<1, false>(a.g, x);
-    hn[4] = nbr_half<2, true>(a.g, x); hn[5] = nbr_half<2, false>(a.g, x);
-    hn[6] = nbr_half<3, true>(a.g, x); hn[7] = nbr_half<3, false>(a.g, x);
-    // neighbour scales (with the time boundary phase) and their largest magnitude per unit
-    float s0[8], s1[8];
-    float m0 = 0.f, m1 = 0.f;
-#pragma unroll
-    for (int d = 0; d < 8; d++) {
-      s0[d] = __ldg(a.in_nrm + (long)hn[d] * upb + lu0);
-      s1[d] = __ldg(a.in_nrm + (long)hn[d] * upb + lu1);
-      m0 = fmaxf(m0, s0[d]);
-      m1 = fmaxf(m1, s1[d]);
-    }
-    const bool tf = a.antiperiodic && x.c[3] == a.g.L[3] - 1, tb = a.antiperiodic && x.c[3] == 0;
-    const float i0 = m0 > 0.f ? 1.f / m0 : 0.f, i1 = m1 > 0.f ? 1.f / m1 : 0.f;
-    float up0[4] = {0.f, 0.f, 0.f, 0.f}, up1[4] = {0.f, 0.f, 0.f, 0.f};
-    float lo0[4] = {0.f, 0.f, 0.f, 0.f}, lo1[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-    for (int mu = 0; mu < 4; mu++) {
-      uint32_t ah0[4] = {0u, 0u, 0u, 0u}, ah1[4] = {0u, 0u, 0u, 0u};   // A for up_k0, up_k1
-      uint32_t ag0[4] = {0u, 0u, 0u, 0u}, ag1[4] = {0u, 0u, 0u, 0u};   // A for lo_k0, lo_k1
-#pragma unroll
-      for (int fb = 0; fb < 2; fb++) {
-        const int d = 2 * mu + fb;
-        const bool fwd = fb == 0;
-        // forward term uses sg = -1 (dagger: +1), backward the opposite
-        const bool neg_sg = fwd ? !dag : dag;
-        float r0 = s0[d] * i0, r1 = s1[d] * i1;
-        if (mu == 3 && (fwd ? tf : tb)) { r0 = -r0; r1 = -r1; }
-        if (c < 3) {
-          const uint4 q0 = __ldg(in4 + ((long)hn[d] * upb + lu0) * 3 + c);
-          const uint4 q1 = __ldg(in4 + ((long)hn[d] * upb + lu1) * 3 + c);
-          const __half2 rr0 = __float2half2_rn(r0), rr1 = __float2half2_rn(r1);
-          uint32_t x0, x1, y0, y1, z0, z1, w0, w1;
-          if (mu == 0) { mma_project<0>(q0, rr0, neg_sg, x0, x1, y0, y1); mma_project<0>(q1, rr1, neg_sg, z0, z1, w0, w1); }
-          else if (mu == 1) { mma_project<1>(q0, rr0, neg_sg, x0, x1, y0, y1); mma_project<1>(q1, rr1, neg_sg, z0, z1, w0, w1); }
-          else if (mu == 2) { mma_project<2>(q0, rr0, neg_sg, x0, x1, y0, y1); mma_project<2>(q1, rr1, neg_sg, z0, z1, w0, w1); }
-          else { mma_project<3>(q0, rr0, neg_sg, x0, x1, y0, y1); mma_project<3>(q1, rr1, neg_sg, z0, z1, w0, w1); }
-          // rows g (unit lu0) and g + 8 (unit lu1); columns of this direction half: 2 fb
-          ah0[2 * fb] = x0; ah0[2 * fb + 1] = z0;
-          ah1[2 * fb] = x1; ah1[2 * fb + 1] = z1;
-          ag0[2 * fb] = y0; ag0[2 * fb + 1] = w0;
-          ag1[2 * fb] = y1; ag1[2 * fb + 1] = w1;
-        }
+    int hn = 0;
+    float kb = a.kappa;
+    if (h < a.g.Vh) {
+      const Site x = make_site(a.g, a.out_par, h);
+      switch (d) {
+        case 0: hn = nbr_half<0, true>(a.g, x); break;
+        case 1: hn = nbr_half<0, false>(a.g, x); break;
+        case 2: hn = nbr_half<1, true>(a.g, x); break;
+        case 3: hn = nbr_half<1, false>(a.g, x); break;
+        case 4: hn = nbr_half<2, true>(a.g, x); break;
+        case 5: hn = nbr_half<2, false>(a.g, x); break;
+        case 6: hn = nbr_half<3, true>(a.g, x); break;
+        default: hn = nbr_half<3, false>(a.g, x); break;
       }
-      const long lf = ((long)a.out_par * a.g.Vh + h) * 4 + mu;
-      const long lb = ((long)(1 - a.out_par) * a.g.Vh + hn[2 * mu + 1]) * 4 + mu;
-      const uint32_t bf = mma_link(a.U16, lf, g, c, true);
-      const uint32_t bb = mma_link(a.U16, lb, g, c, false);
-      mma_m16n8k16(ah0, bf, bb, up0);
-      mma_m16n8k16(ah1, bf, bb, up1);
-      mma_m16n8k16(ag0, bf, bb, lo0);
-      mma_m16n8k16(ag1, bf, bb, lo1);
+      if (a.antiperiodic && ((d == 6 && x.c[3] == a.g.L[3] - 1) || (d == 7 && x.c[3] == 0))) kb = -kb;
     }
-    if (c < 3) {
-      // C row g = unit lu0 (entries 0, 1), row g + 8 = unit lu1 (entries 2, 3); columns 2c, 2c+1 = colour c
-      const int ub0 = (tile << 4) + g, ub1 = ub0 + 8;
-      const int rr0 = lu0 % a.N, rr1 = lu1 % a.N;
-      const bool live0 = a.active == nullptr || a.active[rr0] != 0;
-      const bool live1 = a.active == nullptr || a.active[rr1] != 0;
-      const float f0 = live0 ? m0 : 0.f, f1 = live1 ? m1 : 0.f;
-      float* r0p = sA + (size_t)ub0 * kPadF + 2 * c;
-      float* r1p = sA + (size_t)ub1 * kPadF + 2 * c;
-      r0p[0] = f0 * up0[0]; r0p[1] = f0 * up0[1]; r0p[6] = f0 * up1[0]; r0p[7] = f0 * up1[1];
-      r0p[12] = f0 * lo0[0]; r0p[13] = f0 * lo0[1]; r0p[18] = f0 * lo1[0]; r0p[19] = f0 * lo1[1];
-      r1p[0] = f1 * up0[2]; r1p[1] = f1 * up0[3]; r1p[6] = f1 * up1[2]; r1p[7] = f1 * up1[3];
-      r1p[12] = f1 * lo0[2]; r1p[13] = f1 * lo0[3]; r1p[18] = f1 * lo1[2]; r1p[19] = f1 * lo1[3];
-    }
+    tb.nb[k] = hn;
+    tb.kb[k] = kb;
+  }
+  for (int jj = t.tid; jj < upb; jj += nthr) {
+    const int s = jj / tl.rt, r = blockIdx.y * tl.rt + (jj - s * tl.rt);
+    const bool ok = r < a.N && (a.active == nullptr || a.active[r] != 0);
+    tb.off[jj] = ok ? s * a.N + r : -1;
+  }
+  for (int k = t.tid; k < ntile; k += nthr) {
+    const int j = k / tps;
+    tb.tile[k] = (j << 16) | ((k - j * tps) * 8);
   }
   __syncthreads();
-  float acc[24];
+  const int lane = t.tid & 31, warp = t.tid >> 5, nwarp = nthr >> 5;
+  const int g = lane >> 2, c = lane & 3;
+  const uint32_t upm = (uint32_t)(a.L5 * a.N);    // units of one site in memory
+  const uint4* in4 = reinterpret_cast<const uint4*>(a.in);
+  const bool dag = a.dagger != 0;
+  const uint32_t lb = (uint32_t)((1 - a.out_par) * a.g.Vh);
+  for (int tile = warp; warp < nwarp && tile < ntile; tile += nwarp) {    // whole warps only (mma.sync)
+    const int tj = tb.tile[tile];
+    const int j = tj >> 16;
+    const long h = h0 + j;
+    if (h >= a.g.Vh) continue;                             // uniform over the warp
+    const int jj = (tj & 0xffff) + g;
+    const int off = jj < upb ? tb.off[jj] : -1;
+    const bool live = off >= 0 && c < 3;
+    const uint32_t uo = live ? (uint32_t)off : 0u;
+    const int* nb = tb.nb + 8 * j;
+    const float* kb = tb.kb + 8 * j;
+    // B fragments: forward links of this site, backward links of the neighbours
+    const uint32_t* ff = frag + ((size_t)((uint32_t)(a.out_par * a.g.Vh + h) * 4u) * 2u) * 32u + lane;
+    const uint32_t* fb = frag + 32 + lane;
+    // all loads of the tile first (24 independent loads in flight per lane)
+    uint4 q[8];
+    float sc[8];
+    uint32_t b[8];
 #pragma unroll
-  for (int i = 0; i < 24; i++) acc[i] = sA[(size_t)t.tid * kPadF + i];
+    for (int d = 0; d < 8; d++) {
+      const uint32_t un = (uint32_t)nb[d] * upm + uo;
+      if (live) {
+        q[d] = __ldg(in4 + (size_t)un * 3u + c);
+        sc[d] = __ldg(a.in_nrm + un);
+      } else {
+        q[d] = make_uint4(0u, 0u, 0u, 0u);
+        sc[d] = 0.f;
+      }
+      b[d] = (d & 1) ? __ldg(fb + (size_t)((lb + nb[d]) * 4u + (d >> 1)) * 64u) : __ldg(ff + (d >> 1) * 64);
+    }
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    mma_term<0, true>(q[0], sc[0], b[0], dag, kb[0], acc);
+    mma_term<0, false>(q[1], sc[1], b[1], dag, kb[1], acc);
+    mma_term<1, true>(q[2], sc[2], b[2], dag, kb[2], acc);
+    mma_term<1, false>(q[3], sc[3], b[3], dag, kb[3], acc);
+    mma_term<2, true>(q[4], sc[4], b[4], dag, kb[4], acc);
+    mma_term<2, false>(q[5], sc[5], b[5], dag, kb[5], acc);
+    mma_term<3, true>(q[6], sc[6], b[6], dag, kb[6], acc);
+    mma_term<3, false>(q[7], sc[7], b[7], dag, kb[7], acc);
+    if (live) {
+      float* row = sA + (size_t)(j * upb + jj) * kPadF + 2 * c;
+#pragma unroll
+      for (int sp = 0; sp < 4; sp++) {
+        row[6 * sp] = acc[2 * sp];
+        row[6 * sp + 1] = acc[2 * sp + 1];
+      }
+    }
+  }
+  epilogue<__half, float, EPI, true>(a, tl, t, nullptr, sA);
+}
+
+// Pipelined form of the tensor-core hop (one RHS group, whole 8-unit tiles).
+// The 8 units of a tile are contiguous in memory, so per direction the tile's
+// input is three contiguous runs: 8 spinors (384 B), 8 scales (32 B) and the
+// link fragment (128 B).  Each warp double-buffers its tiles in shared memory:
+// 24 lanes issue the 24 bulk copies (cp.async.bulk, one mbarrier per buffer)
+// of tile k + 1 before it computes tile k, so L2 latency overlaps the work.
+// Every wait is bounded; a warp whose wait runs out records MDWF_TIMEOUT_CODE,
+// waits (bounded) for its own copies still in flight and stops.
+constexpr unsigned kMmaBuf = 8 * (384 + 32 + 128);   // bytes of one tile buffer
+
+template <int EPI>
+__global__ void hop_mma_bulk_kernel(FastArgs<__half, float> a, Tiling tl, const uint32_t* __restrict__ frag,
+                                    StageInfo si) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const Thr t = thread_of(a, tl);
+  const int nthr = tl.threads;
+  const int nwarp = nthr >> 5;
+  const int upb = a.L5 * a.N;                     // units of one site (one RHS group)
+  const int tps = upb >> 3;
+  const int ntile = tl.nsb * tps;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
+  unsigned char* bufs = smem_raw + (((size_t)nwarp * 16 + 127) & ~(size_t)127);
+  float* sA = reinterpret_cast<float*>(bufs + (size_t)nwarp * 2 * kMmaBuf);
+  size_t base = (size_t)nthr * kPadF * sizeof(float);
+  if (base < (size_t)nthr * sizeof(double)) base = (size_t)nthr * sizeof(double);
+  MmaTables tb;
+  tb.nb = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(sA) + base);
+  tb.kb = reinterpret_cast<float*>(tb.nb + 8 * tl.nsb);
+  tb.off = reinterpret_cast<int*>(tb.kb + 8 * tl.nsb);
+  tb.tile = tb.off + upb;
+  const long h0 = (long)blockIdx.x * tl.nsb;
+  for (int k = t.tid; k < 8 * tl.nsb; k += nthr) {
+    const int j = k >> 3, d = k & 7;
+    const long h = h0 + j;
+    int hn = 0;
+    float kb = a.kappa;
+    if (h < a.g.Vh) {
+      const Site x = make_site(a.g, a.out_par, h);
+      switch (d) {
+        case 0: hn = nbr_half<0, true>(a.g, x); break;
+        case 1: hn = nbr_half<0, false>(a.g, x); break;
+        case 2: hn = nbr_half<1, true>(a.g, x); break;
+        case 3: hn = nbr_half<1, false>(a.g, x); break;
+        case 4: hn = nbr_half<2, true>(a.g, x); break;
+        case 5: hn = nbr_half<2, false>(a.g, x); break;
+        case 6: hn = nbr_half<3, true>(a.g, x); break;
+        default: hn = nbr_half<3, false>(a.g, x); break;
+      }
+      if (a.antiperiodic && ((d == 6 && x.c[3] == a.g.L[3] - 1) || (d == 7 && x.c[3] == 0))) kb = -kb;
+    }
+    tb.nb[k] = hn;
+    tb.kb[k] = kb;
+  }
+  for (int jj = t.tid; jj < upb; jj += nthr) {
+    const int r = jj % a.N;
+    tb.off[jj] = (a.active == nullptr || a.active[r] != 0) ? jj : -1;
+  }
+  for (int k = t.tid; k < ntile; k += nthr) {
+    const int j = k / tps;
+    tb.tile[k] = (j << 16) | ((k - j * tps) * 8);
+  }
+  const int lane = t.tid & 31, warp = t.tid >> 5;
+  if (warp < nwarp && lane == 0) {
+    mbar_init(&bars[2 * warp], 1);
+    mbar_init(&bars[2 * warp + 1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
   __syncthreads();
-  epilogue<__half, float, EPI>(a, tl, t, acc, sA);
+  const bool skip = si.err != nullptr && *(volatile int*)si.err != 0;
+  if (warp < nwarp && !skip) {
+    const int g = lane >> 2, c = lane & 3;
+    const uint32_t upm = (uint32_t)upb;
+    const bool dag = a.dagger != 0;
+    const long nsite = (a.g.Vh - h0) < tl.nsb ? (a.g.Vh - h0) : tl.nsb;
+    const int nvalid = (int)nsite * tps;
+    uint64_t* wb = &bars[2 * warp];
+    unsigned char* wbuf = bufs + (size_t)warp * 2 * kMmaBuf;
+    const uint32_t lbase = (uint32_t)((1 - a.out_par) * a.g.Vh);
+    // 24 lanes issue the copies of one tile into buffer bi
+    auto issue = [&](int tile, int bi) {
+      const int tj = tb.tile[tile];
+      const int j = tj >> 16, u0 = tj & 0xffff;
+      if (lane == 0) mbar_expect_tx(&wb[bi], kMmaBuf + si.extra_tx);
+      __syncwarp();
+      if (lane < 24) {
+        const int d = lane / 3, kind = lane - 3 * (lane / 3);
+        const uint32_t un0 = (uint32_t)tb.nb[8 * j + d] * upm + (uint32_t)u0;
+        unsigned char* dst = wbuf + (size_t)bi * kMmaBuf;
+        if (kind == 0) {
+          bulk_g2s(dst + d * 384, a.in + (size_t)un0 * 24u, 384u, &wb[bi]);
+        } else if (kind == 1) {
+          bulk_g2s(dst + 8 * 384 + d * 32, a.in_nrm + un0, 32u, &wb[bi]);
+        } else {
+          const int mu = d >> 1;
+          const uint32_t link = (d & 1) ? (lbase + (uint32_t)tb.nb[8 * j + d]) * 4u + mu
+                                        : (uint32_t)((a.out_par * a.g.Vh + h0 + j) * 4 + mu);
+          bulk_g2s(dst + 8 * (384 + 32) + d * 128, frag + ((size_t)link * 2u + (d & 1)) * 32u, 128u, &wb[bi]);
+        }
+      }
+    };
+    unsigned par0 = 0, par1 = 0;
+    int k = 0;
+    int tile = warp;
+    if (tile < nvalid) issue(tile, 0);
+    for (; tile < nvalid; tile += nwarp, k++) {
+      const int bi = k & 1;
+      const int nxt = tile + nwarp;
+      if (nxt < nvalid) {
+        __syncwarp();                                   // buffer 1 - bi was read by every lane
+        issue(nxt, bi ^ 1);
+      }
+      const unsigned par = bi ? par1 : par0;
+      const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&wb[bi], par, si.budget));
+      if (bi) par1 ^= 1u; else par0 ^= 1u;
+      if (!ok) {
+        if (lane == 0) {
+          if (si.err) atomicExch(si.err, MDWF_TIMEOUT_CODE);
+          if (nxt < nvalid) mbar_wait_bounded(&wb[bi ^ 1], bi ? par0 : par1, si.budget);
+        }
+        __syncwarp();
+        break;
+      }
+      const int tj = tb.tile[tile];
+      const int j = tj >> 16;
+      const int jj = (tj & 0xffff) + g;
+      const bool live = c < 3 && tb.off[jj] >= 0;
+      const unsigned char* src = wbuf + (size_t)bi * kMmaBuf;
+      const uint4* qs = reinterpret_cast<const uint4*>(src);
+      const float* scs = reinterpret_cast<const float*>(src + 8 * 384);
+      const uint32_t* fs = reinterpret_cast<const uint32_t*>(src + 8 * (384 + 32));
+      const float* kb = tb.kb + 8 * j;
+      uint4 q[8];
+      float sc[8];
+      uint32_t b[8];
+#pragma unroll
+      for (int d = 0; d < 8; d++) {
+        q[d] = live ? qs[d * 24 + g * 3 + c] : make_uint4(0u, 0u, 0u, 0u);
+        sc[d] = live ? scs[d * 8 + g] : 0.f;
+        b[d] = fs[d * 32 + lane];
+      }
+      float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      mma_term<0, true>(q[0], sc[0], b[0], dag, kb[0], acc);
+      mma_term<0, false>(q[1], sc[1], b[1], dag, kb[1], acc);
+      mma_term<1, true>(q[2], sc[2], b[2], dag, kb[2], acc);
+      mma_term<1, false>(q[3], sc[3], b[3], dag, kb[3], acc);
+      mma_term<2, true>(q[4], sc[4], b[4], dag, kb[4], acc);
+      mma_term<2, false>(q[5], sc[5], b[5], dag, kb[5], acc);
+      mma_term<3, true>(q[6], sc[6], b[6], dag, kb[6], acc);
+      mma_term<3, false>(q[7], sc[7], b[7], dag, kb[7], acc);
+      if (live) {
+        float* row = sA + (size_t)(j * upb + jj) * kPadF + 2 * c;
+#pragma unroll
+        for (int sp = 0; sp < 4; sp++) {
+          row[6 * sp] = acc[2 * sp];
+          row[6 * sp + 1] = acc[2 * sp + 1];
+        }
+      }
+    }
+  }
+  epilogue<__half, float, EPI, true>(a, tl, t, nullptr, sA);
+}
+
+size_t mma_bulk_smem_bytes(const Tiling& t, int L5) {
+  const size_t nwarp = (size_t)t.threads / 32;
+  size_t base = (size_t)t.threads * kPadF * sizeof(float);
+  if (base < (size_t)t.threads * sizeof(double)) base = (size_t)t.threads * sizeof(double);
+  const size_t upb = (size_t)L5 * t.rt, tps = (upb + 7) / 8;
+  return ((nwarp * 16 + 127) & ~(size_t)127) + nwarp * 2 * kMmaBuf + base +
+         (size_t)t.nsb * 8 * (sizeof(int) + sizeof(float)) + upb * sizeof(int) + t.nsb * tps * sizeof(int);
+}
+
+bool mma_bulk_usable(const FastArgs<__half, float>& a, const Tiling& t) {
+  const int upb = a.L5 * a.N;
+  return t.rt == a.N && t.ngroups == 1 && upb % 8 == 0 && upb % 4 == 0 && t.threads >= 32 && upb < 65536 &&
+         ((uintptr_t)a.in % 16) == 0 && ((uintptr_t)a.in_nrm % 16) == 0 && ((uintptr_t)a.F16 % 16) == 0 &&
+         mma_bulk_smem_bytes(t, a.L5) <= 220 * 1024;
 }
 
 template <int EPI>
-cudaError_t launch_mma_one(const FastArgs<__half, float>& a, const Tiling& t, cudaStream_t st) {
+cudaError_t launch_mma_bulk_one(const FastArgs<__half, float>& a, const Tiling& t, const StageInfo& si,
+                                cudaStream_t st) {
   const dim3 grid((unsigned)t.ntiles, (unsigned)t.ngroups);
   const dim3 block((unsigned)t.rt, (unsigned)a.L5, (unsigned)t.nsb);
-  size_t smem = (size_t)t.threads * kPadF * sizeof(float) + (size_t)t.nsb * sizeof(Site);
+  const size_t smem = mma_bulk_smem_bytes(t, a.L5);
+  cudaError_t e = cudaFuncSetAttribute(hop_mma_bulk_kernel<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  hop_mma_bulk_kernel<EPI><<<grid, block, smem, st>>>(a, t, a.F16, si);
+  return cudaGetLastError();
+}
+
+size_t mma_smem_bytes(const Tiling& t, int L5) {
+  size_t base = (size_t)t.threads * kPadF * sizeof(float);
+  if (base < (size_t)t.threads * sizeof(double)) base = (size_t)t.threads * sizeof(double);
+  const size_t upb = (size_t)L5 * t.rt, tps = (upb + 7) / 8;
+  return base + (size_t)t.nsb * 8 * (sizeof(int) + sizeof(float)) + upb * sizeof(int) + t.nsb * tps * sizeof(int);
+}
+
+template <int EPI>
+cudaError_t launch_mma_one(const FastArgs<__half, float>& a, const Tiling& t, const uint32_t* frag, cudaStream_t st) {
+  const dim3 grid((unsigned)t.ntiles, (unsigned)t.ngroups);
+  const dim3 block((unsigned)t.rt, (unsigned)a.L5, (unsigned)t.nsb);
+  const size_t smem = mma_smem_bytes(t, a.L5);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(hop_mma_kernel<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  hop_mma_kernel<EPI><<<grid, block, smem, st>>>(a, t);
+  hop_mma_kernel<EPI><<<grid, block, smem, st>>>(a, t, frag);
   return cudaGetLastError();
+}
+
+// B fragments of every link: word (link, backward, lane) for lane (g, c) holds
+// rows 2c, 2c+1 and column g of the real form of W = U (forward) or U^+ (backward).
+__global__ void k_link_frags(const double* __restrict__ U, uint32_t* __restrict__ frag, long nlinks) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nlinks * 64) return;
+  const int lane = (int)(i & 31), bwd = (int)((i >> 5) & 1);
+  const long link = i >> 6;
+  const int g = lane >> 2, c = lane & 3, ca = g >> 1;
+  float lo = 0.f, hi = 0.f;
+  if (c < 3 && ca < 3) {
+    // W_ab, a = ca, b = c: U_ab forward, conj(U_ba) backward
+    const double* e = U + link * 18 + 2 * (bwd ? c * 3 + ca : ca * 3 + c);
+    const double re = e[0], im = bwd ? -e[1] : e[1];
+    if (g & 1) { lo = (float)im; hi = (float)re; }
+    else { lo = (float)re; hi = (float)-im; }
+  }
+  const __half2 v = __floats2half2_rn(lo, hi);
+  frag[i] = *reinterpret_cast<const uint32_t*>(&v);
 }
 
 }  // namespace
@@ -869,9 +1177,8 @@ int fast_max_threads() {
 }
 
 bool mma_hop_usable(const Tiling& t, int L5, int N) {
-  const int upb = L5 * N;
-  // whole sites per block, 16-unit tiles inside one site, whole warps
-  return t.rt == N && t.ngroups == 1 && upb % 16 == 0 && t.threads % 32 == 0;
+  // at least one whole warp per block; 8-unit tiles never straddle sites
+  return t.threads >= 32 && mma_smem_bytes(t, L5) <= 200 * 1024 && N >= 1 && L5 >= 1;
 }
 
 int mma_max_threads() {
@@ -887,17 +1194,35 @@ int mma_max_threads() {
   return m;
 }
 
-cudaError_t launch_fast_mma(const FastArgs<__half, float>& a, const Tiling& t, int epi, cudaStream_t st) {
-  if (!mma_hop_usable(t, a.L5, a.N) || a.U16 == nullptr) return cudaErrorInvalidValue;
+cudaError_t launch_fast_mma(const FastArgs<__half, float>& a, const Tiling& t, int epi, cudaStream_t st,
+                            const StageInfo* stage) {
+  if (!mma_hop_usable(t, a.L5, a.N) || a.F16 == nullptr) return cudaErrorInvalidValue;
+  if (stage != nullptr && mma_bulk_usable(a, t)) {
+    switch (epi) {
+      case E_RAW: return launch_mma_bulk_one<E_RAW>(a, t, *stage, st);
+      case E_BAINV: return launch_mma_bulk_one<E_BAINV>(a, t, *stage, st);
+      case E_AINVD_BD: return launch_mma_bulk_one<E_AINVD_BD>(a, t, *stage, st);
+      case E_A_SAME: return launch_mma_bulk_one<E_A_SAME>(a, t, *stage, st);
+      case E_AD_SAME_BD: return launch_mma_bulk_one<E_AD_SAME_BD>(a, t, *stage, st);
+      case E_AINV_SAME: return launch_mma_bulk_one<E_AINV_SAME>(a, t, *stage, st);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (epi) {
-    case E_RAW: return launch_mma_one<E_RAW>(a, t, st);
-    case E_BAINV: return launch_mma_one<E_BAINV>(a, t, st);
-    case E_AINVD_BD: return launch_mma_one<E_AINVD_BD>(a, t, st);
-    case E_A_SAME: return launch_mma_one<E_A_SAME>(a, t, st);
-    case E_AD_SAME_BD: return launch_mma_one<E_AD_SAME_BD>(a, t, st);
-    case E_AINV_SAME: return launch_mma_one<E_AINV_SAME>(a, t, st);
+    case E_RAW: return launch_mma_one<E_RAW>(a, t, a.F16, st);
+    case E_BAINV: return launch_mma_one<E_BAINV>(a, t, a.F16, st);
+    case E_AINVD_BD: return launch_mma_one<E_AINVD_BD>(a, t, a.F16, st);
+    case E_A_SAME: return launch_mma_one<E_A_SAME>(a, t, a.F16, st);
+    case E_AD_SAME_BD: return launch_mma_one<E_AD_SAME_BD>(a, t, a.F16, st);
+    case E_AINV_SAME: return launch_mma_one<E_AINV_SAME>(a, t, a.F16, st);
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t build_link_frags(const double* U64, uint32_t* frag, long nlinks, cudaStream_t st) {
+  const long n = nlinks * 64;
+  k_link_frags<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(U64, frag, nlinks);
+  return cudaGetLastError();
 }
 
 #define MDWF_INST_FAST(S, T)                                                                          \

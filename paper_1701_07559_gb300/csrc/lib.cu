@@ -39,7 +39,7 @@ struct Cfg {
   int anti = 1;
   double* U64 = nullptr;
   float* U32 = nullptr;
-  __half2* U16 = nullptr;   // fp16 links [parity][h][mu][3][3] for the tensor-core hop
+  uint32_t* F16 = nullptr;  // tensor-core hop: fp16 B fragments [parity][h][mu][fwd, bwd][32 lanes]
   Action act;
 };
 
@@ -408,12 +408,12 @@ struct FastOp {
   Prof* prof = nullptr;
   long long* launches = nullptr;
   const StageInfo* stage = nullptr;   // neighbour staging through shared memory, when the tiling allows
-  const __half2* U16 = nullptr;       // fp16 links for the tensor-core hop
+  const uint32_t* F16 = nullptr;      // fp16 link fragments for the tensor-core hop
   bool mma = false;                   // use the tensor-core hop (fp16 storage only)
 
   cudaError_t dispatch(const FastArgs<S, T>& a, int epi) const {
     if constexpr (std::is_same<S, __half>::value) {
-      if (mma) return launch_fast_mma(a, tl, epi, st);
+      if (mma) return launch_fast_mma(a, tl, epi, st, stage);
     }
     return launch_fast<S, T>(a, tl, epi, st, stage);
   }
@@ -423,7 +423,7 @@ struct FastOp {
     FastArgs<S, T> a;
     a.g = g; a.L5 = L5; a.N = N; a.out_par = out_par; a.dagger = dagger; a.antiperiodic = anti;
     a.in = in.v; a.in_nrm = in.n; a.same = same.v; a.same_nrm = same.n; a.add = add.v; a.add_nrm = add.n;
-    a.out = out.v; a.out_nrm = out.n; a.U = U; a.U16 = U16; a.f = f; a.g_same = g_same; a.kappa = kappa;
+    a.out = out.v; a.out_nrm = out.n; a.U = U; a.F16 = F16; a.f = f; a.g_same = g_same; a.kappa = kappa;
     a.active = active;
     a.partials = partials;
     if (launches) *launches += 1;
@@ -469,19 +469,19 @@ void choose_hop(FastOp<S, T>& op, const Cfg* cfg, int nsb_req, int variant, cons
   bool staged = false;
   op.mma = false;
   op.stage = nullptr;
-  op.U16 = cfg->U16;
-  if (variant == HOP_MMA && std::is_same<S, __half>::value && upb % 16 == 0 && cfg->U16) {
-    // whole sites per block and a whole number of warps: nsb a multiple of 32 / gcd(upb, 32)
-    int gcd = upb, b = 32;
-    while (b) { int r = gcd % b; gcd = b; b = r; }
-    const int step = 32 / gcd;
-    int nsb = step;
-    while (nsb * upb < 128) nsb += step;
-    if (nsb_req > 0 && nsb_req % step == 0) nsb = nsb_req;
-    if (nsb <= 64 && nsb * upb <= mma_max_threads()) {
-      op.tl = make_tiling(g.Vh, L5, N, nsb, nsb * upb);
-      if (mma_hop_usable(op.tl, L5, N)) { op.mma = true; return; }
-    }
+  op.F16 = cfg->F16;
+  if (variant == HOP_MMA && std::is_same<S, __half>::value && cfg->F16) {
+    // whole sites per block; prefer a whole number of warps and 128..512 threads
+    int nsb = 0;
+    for (int k = 1; k <= 64 && nsb == 0; k++)
+      if ((k * upb) % 32 == 0 && k * upb >= 128 && k * upb <= 512) nsb = k;
+    if (nsb == 0) nsb = upb >= 128 ? 1 : (128 + upb - 1) / upb;
+    if (nsb_req > 0) nsb = nsb_req;
+    if (nsb > 64) nsb = 64;
+    const int maxthr = mma_max_threads();
+    while (nsb > 1 && nsb * L5 > maxthr) nsb--;
+    op.tl = make_tiling(g.Vh, L5, N, nsb, maxthr);
+    if (mma_hop_usable(op.tl, L5, N)) { op.mma = true; op.stage = stage; return; }
   }
   op.tl = fast_tiling<S>(g, L5, N, nsb_req, &staged, variant == HOP_STAGED);
   op.stage = staged ? stage : nullptr;
@@ -620,8 +620,9 @@ struct BatchSolver {
     stage.budget = wait_budget(c->device, o.wait_timeout_s > 0 ? o.wait_timeout_s : 2.0);
     stage.extra_tx = o.timeout_test ? 16u : 0u;
     stage.err = errw;
-    // the wait-timeout test needs the staged kernel, whose waits it exercises
-    const int variant = o.timeout_test ? HOP_STAGED : o.hop_variant;
+    // the wait-timeout test needs a kernel with waits: the staged one, or the
+    // pipelined tensor-core one when that variant is asked for
+    const int variant = o.timeout_test ? (o.hop_variant == HOP_MMA ? HOP_MMA : HOP_STAGED) : o.hop_variant;
     choose_hop(op64, cf, 0, HOP_DIRECT, &stage);
     choose_hop(op32, cf, nsb, variant == HOP_AUTO ? HOP_DIRECT : variant, &stage);
     choose_hop(opS, cf, nsb, variant, &stage);
@@ -1499,7 +1500,7 @@ int mdwf_destroy(mdwf_ctx* ctx) {
   for (auto& kv : ctx->cfgs) {
     if (kv.second.U64) cudaFree(kv.second.U64);
     if (kv.second.U32) cudaFree(kv.second.U32);
-    if (kv.second.U16) cudaFree(kv.second.U16);
+    if (kv.second.F16) cudaFree(kv.second.F16);
   }
   for (auto& kv : ctx->ws)
     if (kv.second.first) cudaFree(kv.second.first);
@@ -1518,10 +1519,8 @@ int mdwf_load_gauge(mdwf_ctx* ctx, int cfg_id, const double* U, int t_antiperiod
   if (!all_finite(U, n)) return fail(ctx, MDWF_ERR_NONFINITE, "gauge field has NaN/Inf");
   // reorder to [parity][h][mu][18] (FP64) and [parity][h][mu][20] (FP32, padded)
   const size_t n32 = (size_t)g.V * 4 * kLinkStride32;
-  const size_t n16 = (size_t)g.V * 4 * 9;
   std::vector<double> h64(n);
   std::vector<float> h32(n32, 0.0f);
-  std::vector<__half2> h16(n16);
   for (long lex = 0; lex < g.V; lex++) {
     long r = lex;
     int c[4];
@@ -1534,16 +1533,16 @@ int mdwf_load_gauge(mdwf_ctx* ctx, int cfg_id, const double* U, int t_antiperiod
         size_t link = ((size_t)par * g.Vh + h) * 4 + mu;
         h64[link * 18 + k] = v;
         h32[link * kLinkStride32 + k] = (float)v;
-        if (k & 1) h16[link * 9 + k / 2] = __floats2half2_rn((float)U[(lex * 4 + mu) * 18 + k - 1], (float)v);
       }
   }
   CK(cudaSetDevice(ctx->device));
   Cfg& cfg = ctx->cfgs[cfg_id];
   if (!cfg.U64) CK(cudaMalloc(&cfg.U64, sizeof(double) * n));
   if (!cfg.U32) CK(cudaMalloc(&cfg.U32, sizeof(float) * n32));
-  if (!cfg.U16) CK(cudaMalloc(&cfg.U16, sizeof(__half2) * n16));
-  CK(cudaMemcpy(cfg.U16, h16.data(), sizeof(__half2) * n16, cudaMemcpyHostToDevice));
+  if (!cfg.F16) CK(cudaMalloc(&cfg.F16, sizeof(uint32_t) * 64 * (size_t)g.V * 4));
   CK(cudaMemcpy(cfg.U64, h64.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+  CK(build_link_frags(cfg.U64, cfg.F16, (long)g.V * 4, nullptr));
+  CK(cudaDeviceSynchronize());
   CK(cudaMemcpy(cfg.U32, h32.data(), sizeof(float) * n32, cudaMemcpyHostToDevice));
   cfg.has_gauge = true;
   cfg.anti = t_antiperiodic ? 1 : 0;

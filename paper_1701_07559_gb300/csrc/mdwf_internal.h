@@ -329,7 +329,7 @@ struct FastArgs {
   const S* add; const float* add_nrm;
   S* out; float* out_nrm;
   const T* U;
-  const __half2* U16;   // fp16 links [parity][h][mu][3][3] (tensor-core hop), or null
+  const uint32_t* F16;  // tensor-core hop: fp16 B fragments [parity][h][mu][fwd, bwd][lane], or null
   Fifth<T> f;
   T g_same;             // coefficient of A same (E_A_SAME) / A^+ same (E_AD_SAME_BD)
   T kappa;              // coefficient of the hop term
@@ -353,7 +353,10 @@ cudaError_t launch_fast(const FastArgs<S, T>& a, const Tiling& t, int epi, cudaS
 // Tensor-core hop (fp16 storage): usable when a block holds whole sites and L5 N % 8 == 0.
 bool mma_hop_usable(const Tiling& t, int L5, int N);
 int mma_max_threads();
-cudaError_t launch_fast_mma(const FastArgs<__half, float>& a, const Tiling& t, int epi, cudaStream_t st);
+// stage: bound and status word of the waits of the pipelined form (null: unpipelined form)
+cudaError_t launch_fast_mma(const FastArgs<__half, float>& a, const Tiling& t, int epi, cudaStream_t st,
+                            const StageInfo* stage);
+cudaError_t build_link_frags(const double* U64, uint32_t* frag, long nlinks, cudaStream_t st);
 // Shared-memory bytes of a staged launch (0 if the tiling cannot be staged).
 template <typename S, typename T>
 size_t staged_smem_bytes(const Tiling& t, int L5, int N);

@@ -232,19 +232,23 @@ def test_solve_errors():
         M.mdwf_destroy(ctx)
 
 
-def test_bounded_wait_reports_timeout_and_context_survives():
-    """A staged-copy wait that runs out (the test knob makes each barrier expect bytes
+@pytest.mark.parametrize('variant', [2, 3])
+def test_bounded_wait_reports_timeout_and_context_survives(variant):
+    """A bulk-copy wait that runs out (the test knob makes each barrier expect bytes
     that never arrive) ends the solve with MDWF_ERR_TIMEOUT; the same context then
-    solves normally."""
+    solves normally.  Variant 2: the staged CUDA-core hop; 3: the pipelined
+    tensor-core hop (two right-hand sides, so that its 8-unit tiles are whole)."""
     L = Lat(*CASES[0])
     try:
-        b = synth.gaussian_spinor(L.shape, 17)
-        bad = M.mdwf_default_opts(precision='half', timeout_test=1, wait_timeout_s=0.05)
+        bs = [synth.gaussian_spinor(L.shape, 17 + k) for k in range(2)]
+        bad = M.mdwf_default_opts(precision='half', timeout_test=1, wait_timeout_s=0.05, hop_variant=variant)
         with pytest.raises(M.MdwfError) as e:
-            M.mdwf_solve(L.ctx, 0, b, 1e-10, bad)
+            M.mdwf_solve_batch(L.ctx, 0, bs, 1e-10, opts=bad)
         assert e.value.code == M.MDWF_ERR_TIMEOUT
-        x, st = M.mdwf_solve(L.ctx, 0, b, 1e-10, M.mdwf_default_opts(precision='half'))
-        _check_solution(L, b, x, st)
+        xs, st = M.mdwf_solve_batch(L.ctx, 0, bs, 1e-10, opts=M.mdwf_default_opts(precision='half',
+                                                                                     hop_variant=variant))
+        for b, x, s in zip(bs, xs, st):
+            _check_solution(L, b, x, s)
     finally:
         L.close()
 
