@@ -45,7 +45,8 @@ def parse():
                     help="'op': only apply the batched Schur operator (the solver's hop kernels), for profiling")
     ap.add_argument('--lattice', default=None, help="op mode: Lx,Ly,Lz,Lt instead of the workload's 16,16,16,48")
     ap.add_argument('--hop-variant', type=int, default=0,
-                    help='0 automatic, 1 CUDA-core direct loads, 2 CUDA-core staged, 3 tensor-core (fp16)')
+                    help='0 autotuned (CUDA-core forms), 1 CUDA-core direct loads, 2 CUDA-core staged, '
+                         '3 tensor-core (fp16), 4 autotuned including the tensor-core form')
     ap.add_argument('--nsb', type=int, default=0, help='sites per thread block (0: chosen by the library)')
     ap.add_argument('--requests', type=int, default=300, help='serve mode: requests per arrival rate')
     ap.add_argument('--rates', default='0.5,0.9,1.2', help='serve mode: arrival rates as fractions of capacity')
@@ -137,8 +138,8 @@ def ncu_traffic(kernel_key):
     try:
         with open(path) as f:
             rec = json.load(f)
-        src = open(os.path.join(ROOT, 'paper_1701_07559_gb300', 'csrc', 'hop.cu'), 'rb').read()
-        if rec.get('hop_cu_sha256') != hashlib.sha256(src).hexdigest():
+        src = open(os.path.join(ROOT, 'paper_1701_07559_gb300', 'csrc', 'hop_fast.cu'), 'rb').read()
+        if rec.get('hop_fast_cu_sha256') != hashlib.sha256(src).hexdigest():
             return None
         return rec['workloads'][kernel_key]['dram_bytes_per_launch']
     except (OSError, KeyError, ValueError):
@@ -292,6 +293,10 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
     gflops = units * 1320 / hop_avg_s / 1e9
     gpu_launches = sum(s[0]['kernel_launches'] for s in stats)
+    tuned = M.mdwf_autotune(ctx, 0, n, prec, include_tensor_core=args.hop_variant == 4) \
+        if args.hop_variant in (0, 4) and args.nsb == 0 else None
+    kernel_name = {1: 'hop_fast_kernel', 2: 'hop_staged_kernel', 3: 'hop_mma_kernel'}.get(
+        tuned['hop_variant'] if tuned else (args.hop_variant or 1), 'hop_fast_kernel')
 
     # end to end through the host-pointer C ABI call, pinned host buffers
     pin_src = [torch.from_numpy(s).pin_memory().numpy() for s in srcs]
@@ -355,7 +360,8 @@ def run_ours(args):
             'reliable_updates': [s['reliable_updates'] for s in last],
             'fp64_gpu_cg': fp64,
             'speedup_vs_fp64_gpu_cg': (value / fp64['solves_per_s']) if fp64 else None,
-            'dslash': {'kernel': 'hop_kernel<%s>' % prec, 'launches_timed': hop_launches,
+            'autotuned': tuned,
+            'dslash': {'kernel': '%s<%s>' % (kernel_name, prec), 'launches_timed': hop_launches,
                        'avg_launch_us': hop_avg_s * 1e6, 'GB_per_s': achieved, 'eff_GFLOP_per_s': gflops,
                        'units_per_launch': units, 'bytes_per_launch': bytes_per_launch},
             'roofline': {'bound': 'hbm', 'achieved': achieved, 'peak': peak, 'unit': 'GB/s',

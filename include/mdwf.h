@@ -72,10 +72,14 @@ typedef struct {
                             the call with MDWF_ERR_TIMEOUT and leaves the context usable */
   int timeout_test;      /* testing only: 1 makes each staged-copy wait expect bytes that never
                             arrive, so the bound above must end the call with MDWF_ERR_TIMEOUT */
-  int hop_variant;       /* 0: automatic (today the CUDA-core hop with direct loads, the fastest
-                            measured); 1: CUDA-core hop with direct neighbour loads; 2: CUDA-core hop
-                            with neighbours staged in shared memory by bulk copies; 3: tensor-core
-                            colour multiply (fp16 storage, L5 N a multiple of 16), else as 0 */
+  int hop_variant;       /* 0: automatic: the autotuner times the CUDA-core hop forms (direct or
+                            staged neighbour loads, 1..8 sites per block) once per (L5, N, precision)
+                            and context and keeps the fastest; all of them give identical results.
+                            1: CUDA-core hop with direct neighbour loads; 2: CUDA-core hop with
+                            neighbours staged in shared memory by bulk copies; 3: tensor-core colour
+                            multiply (fp16 storage only, else as 1; pipelined through bulk copies
+                            when L5 N is a multiple of 8); 4: as 0 with the tensor-core hop among
+                            the candidates (its rounding differs from the CUDA-core forms) */
   int reserved[2];
 } mdwf_solver_opts;
 
@@ -258,6 +262,15 @@ int mdwf_session_occupied(const mdwf_session* s);
 
 /* mdwf_make_source on device fields (eta4d: V * 24 doubles; src5d: L5 * V * 24), on `stream`. */
 int mdwf_make_source_dev(mdwf_ctx* ctx, int cfg_id, const double* eta4d, double* src5d, void* stream);
+
+/* The autotuner on its own: the inner hop form and sites per block that the
+ * solver uses for n right-hand sides of this configuration at `precision`
+ * (include_tensor_core: also try the tensor-core hop), with its time for one
+ * Mhat + Mhat^+ application.  Runs the timing once per (L5, n, precision,
+ * candidate set) and context, then answers from the cache.  Outputs may be NULL.
+ * Errors: ARG, STATE, NOMEM, CUDA, TIMEOUT. */
+int mdwf_autotune(mdwf_ctx* ctx, int cfg_id, int n, int precision, int include_tensor_core, int* hop_variant,
+                  int* nsb, double* ms_per_pair);
 
 /* Z2 noise 4D source on a device field eta4d (V * 24 doubles), on `stream`:
  * complex element k ([t][z][y][x][spin][colour] order) is +1 or -1 (imaginary

@@ -207,18 +207,18 @@ __device__ __forceinline__ int nbr_half(const Geom& g, const Site& x) {
   return n >> 1;
 }
 
-// One of the eight hopping terms; the neighbour spinor comes either from global
-// memory (sp == nullptr) or from the shared staging buffer sp.
+// One of the eight hopping terms at neighbour half-site hn (bflip: the term
+// crosses the antiperiodic time boundary); the neighbour spinor comes either
+// from global memory (sp == nullptr) or from the shared staging buffer sp.
 template <int MU, bool FWD, typename S, typename T>
-__device__ __forceinline__ void hop_term(const FastArgs<S, T>& a, const Site& x, long h, int s, int r, const S* sp,
-                                         float snrm, T* acc) {
-  const int hn = nbr_half<MU, FWD>(a.g, x);
+__device__ __forceinline__ void hop_term_at(const FastArgs<S, T>& a, int hn, bool bflip, long h, int s, int r,
+                                            const S* sp, float snrm, T* acc) {
   const T sg = (a.dagger ? T(1) : T(-1)) * (FWD ? T(1) : T(-1));
   T hh[12], chi[12], l[18];
   T f;
   if (sp == nullptr) f = Proj<MU, S, T>::global(a.in, a.in_nrm, ((long)hn * a.L5 + s) * a.N + r, sg, hh);
   else f = Proj<MU, S, T>::shared(sp, snrm, sg, hh);
-  if (MU == 3 && a.antiperiodic && (FWD ? x.c[3] == a.g.L[3] - 1 : x.c[3] == 0)) f = -f;
+  if (bflip) f = -f;
   if (FWD) {
     load_link<T>(a.U, ((long)a.out_par * a.g.Vh + h) * 4 + MU, l);
     su3_mul<T, false>(l, hh, chi);
@@ -229,6 +229,13 @@ __device__ __forceinline__ void hop_term(const FastArgs<S, T>& a, const Site& x,
     su3_mul<T, true>(l, hh + 6, chi + 6);
   }
   reconstruct<MU, T>(chi, f, f * sg, acc);
+}
+
+template <int MU, bool FWD, typename S, typename T>
+__device__ __forceinline__ void hop_term(const FastArgs<S, T>& a, const Site& x, long h, int s, int r, const S* sp,
+                                         float snrm, T* acc) {
+  const bool bflip = MU == 3 && a.antiperiodic && (FWD ? x.c[3] == a.g.L[3] - 1 : x.c[3] == 0);
+  hop_term_at<MU, FWD, S, T>(a, nbr_half<MU, FWD>(a.g, x), bflip, h, s, r, sp, snrm, acc);
 }
 
 // A (dag = false) or A^+ (dag = true) of the stored field `same` at (h, s, r):
@@ -518,23 +525,60 @@ __device__ __forceinline__ void epilogue(const FastArgs<S, T>& a, const Tiling& 
   }
 }
 
+__device__ __forceinline__ int nbr_half_any(const Geom& g, const Site& x, int d) {
+  switch (d) {
+    case 0: return nbr_half<0, true>(g, x);
+    case 1: return nbr_half<0, false>(g, x);
+    case 2: return nbr_half<1, true>(g, x);
+    case 3: return nbr_half<1, false>(g, x);
+    case 4: return nbr_half<2, true>(g, x);
+    case 5: return nbr_half<2, false>(g, x);
+    case 6: return nbr_half<3, true>(g, x);
+    default: return nbr_half<3, false>(g, x);
+  }
+}
+
+// Shared memory of the direct kernel: the epilogue tile (threads x kPadF reals,
+// at least threads doubles), then per (site, direction) the neighbour half-site
+// index with the time-boundary flag in bit 31.
+template <typename T>
+__host__ __device__ __forceinline__ size_t direct_tile_bytes(int threads) {
+  size_t b = (size_t)threads * kPadF * sizeof(T);
+  if (b < (size_t)threads * sizeof(double)) b = (size_t)threads * sizeof(double);
+  return b;
+}
+
 template <typename S, typename T, int EPI>
 __global__ void hop_fast_kernel(FastArgs<S, T> a, Tiling tl) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const Thr t = thread_of(a, tl);
+  int* sNb = reinterpret_cast<int*>(smem_raw + direct_tile_bytes<T>(tl.threads));
+  const long h0 = (long)blockIdx.x * tl.nsb;
+  for (int k = t.tid; k < 8 * tl.nsb; k += tl.threads) {
+    const int j = k >> 3, d = k & 7;
+    int v = 0;
+    if (h0 + j < a.g.Vh) {
+      const Site x = make_site(a.g, a.out_par, h0 + j);
+      v = nbr_half_any(a.g, x, d);
+      if (a.antiperiodic && ((d == 6 && x.c[3] == a.g.L[3] - 1) || (d == 7 && x.c[3] == 0))) v |= (int)0x80000000u;
+    }
+    sNb[k] = v;
+  }
+  __syncthreads();
   T acc[24];
 #pragma unroll
   for (int i = 0; i < 24; i++) acc[i] = 0;
   if (t.act) {
-    const Site x = make_site(a.g, a.out_par, t.h);
-    hop_term<0, true, S, T>(a, x, t.h, t.s, t.r, nullptr, 1.f, acc);
-    hop_term<0, false, S, T>(a, x, t.h, t.s, t.r, nullptr, 1.f, acc);
-    hop_term<1, true, S, T>(a, x, t.h, t.s, t.r, nullptr, 1.f, acc);
-    hop_term<1, false, S, T>(a, x, t.h, t.s, t.r, nullptr, 1.f, acc);
-    hop_term<2, true, S, T>(a, x, t.h, t.s, t.r, nullptr, 1.f, acc);
-    hop_term<2, false, S, T>(a, x, t.h, t.s, t.r, nullptr, 1.f, acc);
-    hop_term<3, true, S, T>(a, x, t.h, t.s, t.r, nullptr, 1.f, acc);
-    hop_term<3, false, S, T>(a, x, t.h, t.s, t.r, nullptr, 1.f, acc);
+    const int* nb = sNb + 8 * t.site_l;
+    hop_term_at<0, true, S, T>(a, nb[0], false, t.h, t.s, t.r, nullptr, 1.f, acc);
+    hop_term_at<0, false, S, T>(a, nb[1], false, t.h, t.s, t.r, nullptr, 1.f, acc);
+    hop_term_at<1, true, S, T>(a, nb[2], false, t.h, t.s, t.r, nullptr, 1.f, acc);
+    hop_term_at<1, false, S, T>(a, nb[3], false, t.h, t.s, t.r, nullptr, 1.f, acc);
+    hop_term_at<2, true, S, T>(a, nb[4], false, t.h, t.s, t.r, nullptr, 1.f, acc);
+    hop_term_at<2, false, S, T>(a, nb[5], false, t.h, t.s, t.r, nullptr, 1.f, acc);
+    const int n6 = nb[6], n7 = nb[7];
+    hop_term_at<3, true, S, T>(a, n6 & 0x7fffffff, n6 < 0, t.h, t.s, t.r, nullptr, 1.f, acc);
+    hop_term_at<3, false, S, T>(a, n7 & 0x7fffffff, n7 < 0, t.h, t.s, t.r, nullptr, 1.f, acc);
   }
   epilogue<S, T, EPI>(a, tl, t, acc, reinterpret_cast<T*>(smem_raw));
 }
@@ -575,18 +619,6 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
   return true;
 }
 
-__device__ __forceinline__ int nbr_half_any(const Geom& g, const Site& x, int d) {
-  switch (d) {
-    case 0: return nbr_half<0, true>(g, x);
-    case 1: return nbr_half<0, false>(g, x);
-    case 2: return nbr_half<1, true>(g, x);
-    case 3: return nbr_half<1, false>(g, x);
-    case 4: return nbr_half<2, true>(g, x);
-    case 5: return nbr_half<2, false>(g, x);
-    case 6: return nbr_half<3, true>(g, x);
-    default: return nbr_half<3, false>(g, x);
-  }
-}
 
 template <int D, typename S, typename T>
 __device__ __forceinline__ bool staged_term(const FastArgs<S, T>& a, const Tiling& tl, const StageInfo& si,
@@ -691,8 +723,7 @@ cudaError_t launch_one(const FastArgs<S, T>& a, const Tiling& t, cudaStream_t st
     hop_staged_kernel<S, T, EPI><<<grid, block, smem, st>>>(a, t, si);
     return cudaGetLastError();
   }
-  size_t smem = (size_t)t.threads * kPadF * sizeof(T);
-  if (smem < (size_t)t.threads * sizeof(double)) smem = (size_t)t.threads * sizeof(double);
+  const size_t smem = direct_tile_bytes<T>(t.threads) + (size_t)t.nsb * 8 * sizeof(int);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(hop_fast_kernel<S, T, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);

@@ -17,6 +17,7 @@
 #include <cstdio>
 #include <cstring>
 #include <initializer_list>
+#include <array>
 #include <map>
 #include <string>
 #include <type_traits>
@@ -51,6 +52,8 @@ struct mdwf_ctx {
   cudaStream_t stream = nullptr;
   std::map<std::string, std::pair<void*, size_t>> ws;  // reusable device workspace
   int next_session = 0;
+  // autotuned hop form per (L5, N, storage precision, candidate set): {variant, nsb}, best ms
+  std::map<std::array<int, 4>, std::pair<std::array<int, 2>, double>> tuned;
 };
 
 struct SessionBase {
@@ -456,7 +459,7 @@ struct FastOp {
 // neighbour sites in shared memory when a block can hold whole sites (all N
 // slots of nsb sites, at most ~200 KB of staging); FP64 runs unstaged.
 // Hop kernel variants: 0 automatic, 1 CUDA-core direct loads, 2 CUDA-core staged, 3 tensor-core (fp16).
-enum { HOP_AUTO = 0, HOP_DIRECT = 1, HOP_STAGED = 2, HOP_MMA = 3 };
+enum { HOP_AUTO = 0, HOP_DIRECT = 1, HOP_STAGED = 2, HOP_MMA = 3, HOP_TUNE_ALL = 4 };
 
 template <typename S>
 Tiling fast_tiling(const Geom& g, int L5, int N, int nsb_req, bool* staged, bool allow_staging);
@@ -587,6 +590,7 @@ struct BatchSolver {
   StageInfo stage;
   int* errw = nullptr;            // device status word of the bounded waits
   std::string wsp;                // prefix of this solver's workspace names (sessions own theirs)
+  int tune_request = -1;          // HOP_AUTO / HOP_TUNE_ALL: pick the inner hop form by timing (tune())
 
   ~BatchSolver() { if (graph) cudaGraphExecDestroy(graph); }
 
@@ -624,11 +628,11 @@ struct BatchSolver {
     // pipelined tensor-core one when that variant is asked for
     const int variant = o.timeout_test ? (o.hop_variant == HOP_MMA ? HOP_MMA : HOP_STAGED) : o.hop_variant;
     choose_hop(op64, cf, 0, HOP_DIRECT, &stage);
-    choose_hop(op32, cf, nsb, variant == HOP_AUTO ? HOP_DIRECT : variant, &stage);
-    choose_hop(opS, cf, nsb, variant, &stage);
+    choose_hop(op32, cf, nsb, (variant == HOP_AUTO || variant == HOP_TUNE_ALL) ? HOP_DIRECT : variant, &stage);
+    choose_hop(opS, cf, nsb, (variant == HOP_AUTO || variant == HOP_TUNE_ALL) ? HOP_DIRECT : variant, &stage);
+    tune_request = (variant == HOP_AUTO || variant == HOP_TUNE_ALL) && nsb == 0 ? variant : -1;
     op64.launches = op32.launches = opS.launches = &launches;
     profiling = profile;
-    if (profile) opS.prof = &prof;
     F<double>* f64[] = {&b_e, &b_o, &x_acc, &x_hi, &x_o, &bhat, &rho64, &u64, &t64};
     const char* n64[] = {"b_e", "b_o", "x_acc", "x_hi", "x_o", "bhat", "rho64", "u64", "t64"};
     for (int i = 0; i < 9; i++) CK(ws_field<double>(c, wsp + n64[i], units, f64[i]));
@@ -657,6 +661,77 @@ struct BatchSolver {
     CK(cudaMemsetAsync(xlo.v, 0, sizeof(SX) * 24 * (size_t)units, st));
     CK(cudaMemsetAsync(p.v, 0, sizeof(S) * 24 * (size_t)units, st));
     if (p.n) CK(cudaMemsetAsync(p.n, 0, sizeof(float) * (size_t)units, st));
+    if (tune_request >= 0) {
+      // the timing runs write t, q, r and the partial sums only; p is zeroed again after it
+      if (int rc = tune(tune_request)) return rc;
+      CK(cudaMemsetAsync(p.v, 0, sizeof(S) * 24 * (size_t)units, st));
+      if (p.n) CK(cudaMemsetAsync(p.n, 0, sizeof(float) * (size_t)units, st));
+    }
+    if (profile) opS.prof = &prof;
+    return MDWF_OK;
+  }
+
+  // Autotuner: time Mhat + Mhat^+ of the inner precision over the candidate hop
+  // forms and block shapes on this solver's own fields, keep the fastest, and
+  // remember it in the context for (L5, N, precision, candidate set).  HOP_AUTO
+  // tries only forms with the same arithmetic (CUDA-core hop, direct or staged
+  // neighbours, 1..8 sites per block), so the choice never changes a result;
+  // HOP_TUNE_ALL adds the tensor-core hop.
+  int tune(int which, int* variant_out = nullptr, int* nsb_out = nullptr, double* ms_out = nullptr) {
+    mdwf_ctx* ctx = this->ctx;
+    const int prec = kFP64 ? MDWF_PREC_DOUBLE : std::is_same<S, float>::value ? MDWF_PREC_SINGLE
+                   : std::is_same<S, __half>::value ? MDWF_PREC_HALF : MDWF_PREC_BF16;
+    const std::array<int, 4> key = {L5, N, prec, which == HOP_TUNE_ALL ? 1 : 0};
+    auto it = ctx->tuned.find(key);
+    if (it == ctx->tuned.end()) {
+      std::vector<std::array<int, 2>> cand;
+      for (int nsbc : {1, 2, 4, 8})
+        if (nsbc * L5 <= 1024) cand.push_back({HOP_DIRECT, nsbc});
+      if (!kFP64) cand.push_back({HOP_STAGED, 0});
+      if (which == HOP_TUNE_ALL && std::is_same<S, __half>::value) cand.push_back({HOP_MMA, 0});
+      cudaStream_t st = op64.st;
+      cudaEvent_t e0, e1;
+      CK(cudaEventCreate(&e0));
+      CK(cudaEventCreate(&e1));
+      const long long keep = launches;
+      Prof* keep_prof = opS.prof;
+      opS.prof = nullptr;
+      std::array<int, 2> best = {HOP_DIRECT, 0};
+      double best_ms = 1e300;
+      int rc = MDWF_OK;
+      for (const auto& cnd : cand) {
+        choose_hop(opS, cfg, cnd[1], cnd[0], &stage);
+        if (cnd[0] == HOP_MMA && !opS.mma) continue;
+        if (cnd[0] == HOP_STAGED && opS.stage == nullptr) continue;
+        if (cnd[0] == HOP_DIRECT && opS.tl.nsb != cnd[1]) continue;
+        float ms = 0.f;
+        cudaError_t e = cudaSuccess;
+        for (int rep = 0; rep < 3 && e == cudaSuccess; rep++) {
+          if (rep == 1) e = cudaEventRecord(e0, st);
+          if (e == cudaSuccess) e = opS.mhat(p, u, t, q, nullptr, nullptr);
+          if (e == cudaSuccess) e = opS.mhat_dag(q, t, r, nullptr, nullptr);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) { rc = fail(ctx, MDWF_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e)); break; }
+        if (ms / 2.0 < best_ms) { best_ms = ms / 2.0; best = cnd; }
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      launches = keep;
+      opS.prof = keep_prof;
+      if (rc) return rc;
+      int herr = 0;
+      CK(cudaMemcpyAsync(&herr, errw, sizeof(int), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      if (herr) return fail(ctx, MDWF_ERR_TIMEOUT, "autotune: a bounded device wait ran out");
+      it = ctx->tuned.emplace(key, std::make_pair(best, best_ms)).first;
+    }
+    choose_hop(opS, cfg, it->second.first[1], it->second.first[0], &stage);
+    if (variant_out) *variant_out = it->second.first[0];
+    if (nsb_out) *nsb_out = opS.tl.nsb;
+    if (ms_out) *ms_out = it->second.second;
     return MDWF_OK;
   }
 
@@ -1804,6 +1879,36 @@ int mdwf_z2_source_dev(mdwf_ctx* ctx, unsigned long long seed, double* eta4d, vo
   CK(cudaSetDevice(ctx->device));
   CK(z2_source(seed, eta4d, ctx->g.V, pick_stream(ctx, stream)));
   return MDWF_OK;
+}
+
+int mdwf_autotune(mdwf_ctx* ctx, int cfg_id, int n, int precision, int include_tensor_core, int* hop_variant,
+                  int* nsb, double* ms_per_pair) {
+  if (!ctx) return MDWF_ERR_ARG;
+  Cfg* cfg;
+  int rc = check_cfg(ctx, cfg_id, &cfg);
+  if (rc) return rc;
+  if (n < 1 || n > 1024) return fail(ctx, MDWF_ERR_ARG, "autotune: bad n");
+  CK(cudaSetDevice(ctx->device));
+  mdwf_solver_opts o;
+  mdwf_default_opts(&o);
+  o.precision = precision;
+  o.hop_variant = include_tensor_core ? HOP_TUNE_ALL : HOP_AUTO;
+  std::vector<double> m(n, cfg->act.mf);
+  auto run = [&](auto& sv) -> int {
+    sv.wsp = "autotune.";
+    int r = sv.init(ctx, cfg, m, 0, false, o, ctx->stream);
+    if (r) return r;
+    return sv.tune(o.hop_variant, hop_variant, nsb, ms_per_pair);
+  };
+  switch (precision) {
+    case MDWF_PREC_DOUBLE: { BatchSolver<double> sv; rc = run(sv); break; }
+    case MDWF_PREC_SINGLE: { BatchSolver<float> sv; rc = run(sv); break; }
+    case MDWF_PREC_HALF: { BatchSolver<__half> sv; rc = run(sv); break; }
+    case MDWF_PREC_BF16: { BatchSolver<__nv_bfloat16> sv; rc = run(sv); break; }
+    default: return fail(ctx, MDWF_ERR_ARG, "autotune: unknown precision");
+  }
+  ws_release_prefix(ctx, "autotune.");
+  return rc;
 }
 
 int mdwf_extract_prop4d(const double* x5d, const int dims[4], int L5, double* q4d) {

@@ -101,6 +101,7 @@ _sig = {
     'mdwf_session_occupied': (_I, [_P]),
     'mdwf_make_source_dev': (_I, [_P, _I, _P, _P, _P]),
     'mdwf_z2_source_dev': (_I, [_P, ctypes.c_ulonglong, _P, _P]),
+    'mdwf_autotune': (_I, [_P, _I, _I, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_D)]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(_lib, _name)
@@ -311,7 +312,7 @@ def mdwf_solve_batch_dev(ctx, cfg_id, srcs, xs, tol, masses=None, opts=None, str
     return [s.as_dict() for s in st]
 
 
-HOP_AUTO, HOP_DIRECT, HOP_STAGED = 0, 1, 2
+HOP_AUTO, HOP_DIRECT, HOP_STAGED, HOP_MMA, HOP_TUNE_ALL = 0, 1, 2, 3, 4
 
 
 def mdwf_apply_schur_batch_dev(ctx, cfg_id, ins, outs, masses=None, dagger=0, precision=MDWF_PREC_HALF,
@@ -386,6 +387,17 @@ def mdwf_make_source_dev(ctx, cfg_id, eta, out, stream=None):
     sh = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
     _check(ctx, _lib.mdwf_make_source_dev(ctx.handle, int(cfg_id), _dev_ptr(eta, shape4),
                                           _dev_ptr(out, _shape5(ctx, cfg_id)), sh))
+
+
+def mdwf_autotune(ctx, cfg_id, n, precision=MDWF_PREC_HALF, include_tensor_core=False):
+    """The inner hop form the solver picks for n right-hand sides: returns
+    {'hop_variant', 'nsb', 'ms_per_pair'} (ms for one Mhat + Mhat^+ application)."""
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    v, nsb, ms = _I(), _I(), _D()
+    _check(ctx, _lib.mdwf_autotune(ctx.handle, int(cfg_id), int(n), int(precision), int(bool(include_tensor_core)),
+                                   ctypes.byref(v), ctypes.byref(nsb), ctypes.byref(ms)))
+    return {'hop_variant': v.value, 'nsb': nsb.value, 'ms_per_pair': ms.value}
 
 
 def mdwf_z2_source_dev(ctx, seed, eta, stream=None):

@@ -283,3 +283,26 @@ def test_schur_batch_multi_rhs(precision, tol, dagger, variant, L5, masses):
             assert _rel(o.cpu().numpy(), ref) < tol
     finally:
         M.mdwf_destroy(ctx)
+
+
+def test_autotuner_choice_is_cached_and_keeps_results():
+    """The autotuner picks a hop form per (L5, N, precision); its default candidate
+    set shares one arithmetic, so a solve gives the same bits with the tuned form
+    as with a fixed one."""
+    L = Lat(*CASES[3])
+    try:
+        t1 = M.mdwf_autotune(L.ctx, 0, 3, 'half')
+        t2 = M.mdwf_autotune(L.ctx, 0, 3, 'half')
+        assert t1 == t2 and t1['hop_variant'] in (M.HOP_DIRECT, M.HOP_STAGED) and t1['ms_per_pair'] > 0
+        ta = M.mdwf_autotune(L.ctx, 0, 3, 'half', include_tensor_core=True)
+        assert ta['hop_variant'] in (M.HOP_DIRECT, M.HOP_STAGED, M.HOP_MMA)
+        bs = [synth.gaussian_spinor(L.shape, 40 + k) for k in range(3)]
+        xa, sa = M.mdwf_solve_batch(L.ctx, 0, bs, 1e-10, opts=M.mdwf_default_opts(precision='half'))
+        xd, sd = M.mdwf_solve_batch(L.ctx, 0, bs, 1e-10, opts=M.mdwf_default_opts(precision='half', hop_variant=1,
+                                                                                      nsb=1))
+        for x, y in zip(xa, xd):
+            assert np.array_equal(x, y)
+        for b, x, s in zip(bs, xa, sa):
+            _check_solution(L, b, x, s)
+    finally:
+        L.close()
