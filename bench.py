@@ -267,12 +267,10 @@ def run_ours(args):
     wall = time.perf_counter() - t0
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_s = sum(step_ms) / 1e3
-    if dist is not None:
-        t = torch.tensor([total_s], device='cuda', dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = n * args.steps * world / total_s
+    from paper_1701_07559_gb300 import replicas
+    # independent replicas: solves of all ranks over the slowest rank's time
+    value = replicas.job_throughput(n * args.steps, sum(step_ms) / 1e3, dist, 'cuda')
+    total_s = replicas.max_over_ranks(sum(step_ms) / 1e3, dist, 'cuda')
 
     # correctness of what was timed: FP64 true residual of the last step, and the
     # oracle's own D on one solution (rank 0)
@@ -310,12 +308,7 @@ def run_ours(args):
         t1 = time.perf_counter()
         M.mdwf_solve_batch(ctx, 0, pin_src, W['tol'], opts=opts_e2e, out=pin_x)
         e2e_t.append(time.perf_counter() - t1)
-    e2e_total = sum(e2e_t)
-    if dist is not None:
-        t = torch.tensor([e2e_total], device='cuda', dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_value = n * args.steps * world / e2e_total
+    e2e_value = replicas.job_throughput(n * args.steps, sum(e2e_t), dist, 'cuda')
     field_bytes = L5 * V * 24 * 8
 
     # plain FP64 single-RHS GPU CG on the first source (the baseline to beat)
