@@ -146,6 +146,16 @@ def ncu_traffic(kernel_key):
         return None
 
 
+def flowed_links(M, dims, seed, eps, flow_t, flow_eps, device=0):
+    """Random links exp(i eps H) (host generator) flowed to flow_t on the device."""
+    import synth
+    ctx = M.mdwf_create(dims, device)
+    try:
+        return M.flowed_gauge_dev(ctx, synth.random_gauge(dims, seed, eps), flow_t, flow_eps)
+    finally:
+        M.mdwf_destroy(ctx)
+
+
 def make_inputs(M, ctx, W, nsrc):
     import synth
     srcs = []
@@ -232,7 +242,7 @@ def run_ours(args):
     from paper_1701_07559_gb300 import mdwf as M
     W = WORKLOAD
     prec = args.precision
-    U = synth.flowed_gauge(W['dims'], W['seed'], W['eps'], W['flow_t'], W['flow_eps'])
+    U = flowed_links(M, W['dims'], W['seed'], W['eps'], W['flow_t'], W['flow_eps'], local)
     ctx = M.mdwf_create(W['dims'], local)
     M.mdwf_load_gauge(ctx, 0, U, 1)
     M.mdwf_set_action(ctx, 0, W['M5'], W['b5'], W['c5'], W['mf'], W['L5'])
@@ -440,8 +450,8 @@ def run_serve(args):
     import torch
     import __graft_entry__
     __graft_entry__.build()
-    import synth
     from paper_1701_07559_gb300 import serving
+    from paper_1701_07559_gb300 import mdwf as M
     torch.cuda.set_device(0)
     budget = int(args.hbm_budget_gb * 1e9) if args.hbm_budget_gb > 0 else None
     srv = serving.Server(device=0, hbm_budget=budget, tol=1e-10, precision=args.precision, max_slots=args.slots)
@@ -452,7 +462,7 @@ def run_serve(args):
         d = tuple(int(v) for v in lat.split(','))
         l5 = int(l5)
         M5, b5, c5 = SERVE_ACTIONS.get(l5, (1.3, 1.5, 0.5))
-        U = synth.flowed_gauge(d, 5 + i, 0.4, 1.0, 0.01)
+        U = flowed_links(M, d, 5 + i, 0.4, 1.0, 0.01)
         name = '%dx%dx%dx%d L5=%d' % (d + (l5,))
         srv.add_config(name, d, U, M5, b5, c5, SERVE_MASSES[1], l5)
         names.append(name)

@@ -272,6 +272,19 @@ int mdwf_make_source_dev(mdwf_ctx* ctx, int cfg_id, const double* eta4d, double*
 int mdwf_autotune(mdwf_ctx* ctx, int cfg_id, int n, int precision, int include_tensor_core, int* hop_variant,
                   int* nsb, double* ms_per_pair);
 
+/* Wilson (gradient) flow of a gauge field on the device, in place: U is a
+ * device array in the mdwf_load_gauge layout (V * 4 * 18 doubles) of this
+ * context's lattice; nsteps steps of size eps of Luscher's three-stage
+ * Runge-Kutta scheme for dV/dt = -P_TA(Omega) V (Wilson plaquette action), in
+ * FP64 (the smoothing of Sec. III, flow time nsteps * eps).  Input preparation:
+ * load the result with mdwf_load_gauge.  Holds 3 * 4V * 18 doubles of scratch
+ * during the call.  Errors: ARG, NOMEM, CUDA. */
+int mdwf_wilson_flow_dev(mdwf_ctx* ctx, double* U, double eps, int nsteps, void* stream);
+
+/* Average plaquette (1/(18 V)) sum_{x, mu<nu} Re tr P_mu_nu(x) of a device gauge
+ * field U (layout as above); synchronous, result in *plaq (host). */
+int mdwf_plaquette_dev(mdwf_ctx* ctx, const double* U, double* plaq);
+
 /* Z2 noise 4D source on a device field eta4d (V * 24 doubles), on `stream`:
  * complex element k ([t][z][y][x][spin][colour] order) is +1 or -1 (imaginary
  * part 0) by the top bit of the k-th output of SplitMix64 started from `seed`

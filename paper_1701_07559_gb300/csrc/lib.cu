@@ -1911,6 +1911,36 @@ int mdwf_autotune(mdwf_ctx* ctx, int cfg_id, int n, int precision, int include_t
   return rc;
 }
 
+int mdwf_wilson_flow_dev(mdwf_ctx* ctx, double* U, double eps, int nsteps, void* stream) {
+  if (!ctx) return MDWF_ERR_ARG;
+  if (!U || nsteps < 0 || !std::isfinite(eps)) return fail(ctx, MDWF_ERR_ARG, "wilson_flow_dev: bad arguments");
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = pick_stream(ctx, stream);
+  const size_t nlink = (size_t)ctx->g.V * 4;
+  cudaError_t e = cudaSuccess;
+  double* Z = (double*)ws_get(ctx, "flow.Z", sizeof(double) * 54 * nlink, &e);
+  CK(e);
+  CK(wilson_flow(U, ctx->g.L, eps, nsteps, Z, st));
+  CK(cudaStreamSynchronize(st));
+  ws_release_prefix(ctx, "flow.");
+  return MDWF_OK;
+}
+
+int mdwf_plaquette_dev(mdwf_ctx* ctx, const double* U, double* plaq) {
+  if (!ctx) return MDWF_ERR_ARG;
+  if (!U || !plaq) return fail(ctx, MDWF_ERR_ARG, "plaquette_dev: null pointer");
+  CK(cudaSetDevice(ctx->device));
+  cudaError_t e = cudaSuccess;
+  double* part = (double*)ws_get(ctx, "plaq.part", sizeof(double) * (ctx->g.V + 1), &e);
+  CK(e);
+  CK(plaquette(U, ctx->g.L, part + 1, part, ctx->stream));
+  double tot = 0.0;
+  CK(cudaMemcpyAsync(&tot, part, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  *plaq = tot / (18.0 * (double)ctx->g.V);
+  return MDWF_OK;
+}
+
 int mdwf_extract_prop4d(const double* x5d, const int dims[4], int L5, double* q4d) {
   if (!x5d || !dims || !q4d || L5 < 1) return MDWF_ERR_ARG;
   long V = 1;

@@ -357,6 +357,10 @@ int mma_max_threads();
 cudaError_t launch_fast_mma(const FastArgs<__half, float>& a, const Tiling& t, int epi, cudaStream_t st,
                             const StageInfo* stage);
 cudaError_t build_link_frags(const double* U64, uint32_t* frag, long nlinks, cudaStream_t st);
+// Wilson flow (flow.cu): U in the C ABI gauge layout, Z: workspace of 3 * 4V * 18 doubles.
+cudaError_t wilson_flow(double* U, const int L[4], double eps, int nsteps, double* Z, cudaStream_t st);
+// Sum over sites of Re tr of the six plaquettes into *out (device); part: V doubles of workspace.
+cudaError_t plaquette(const double* U, const int L[4], double* part, double* out, cudaStream_t st);
 // Shared-memory bytes of a staged launch (0 if the tiling cannot be staged).
 template <typename S, typename T>
 size_t staged_smem_bytes(const Tiling& t, int L5, int N);

@@ -101,6 +101,8 @@ _sig = {
     'mdwf_session_occupied': (_I, [_P]),
     'mdwf_make_source_dev': (_I, [_P, _I, _P, _P, _P]),
     'mdwf_z2_source_dev': (_I, [_P, ctypes.c_ulonglong, _P, _P]),
+    'mdwf_wilson_flow_dev': (_I, [_P, _P, _D, _I, _P]),
+    'mdwf_plaquette_dev': (_I, [_P, _P, ctypes.POINTER(_D)]),
     'mdwf_autotune': (_I, [_P, _I, _I, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_D)]),
 }
 for _name, (_res, _args) in _sig.items():
@@ -387,6 +389,33 @@ def mdwf_make_source_dev(ctx, cfg_id, eta, out, stream=None):
     sh = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
     _check(ctx, _lib.mdwf_make_source_dev(ctx.handle, int(cfg_id), _dev_ptr(eta, shape4),
                                           _dev_ptr(out, _shape5(ctx, cfg_id)), sh))
+
+
+def _gauge_dev(ctx, U):
+    d = ctx.dims
+    return _dev_ptr(U, (d[3], d[2], d[1], d[0], 4, 3, 3))
+
+
+def mdwf_wilson_flow_dev(ctx, U, eps, nsteps, stream=None):
+    """Wilson flow (Luscher RK3, FP64) of a device gauge field (torch complex128
+    [t, z, y, x, mu, 3, 3]) in place: nsteps steps of size eps."""
+    sh = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+    _check(ctx, _lib.mdwf_wilson_flow_dev(ctx.handle, _gauge_dev(ctx, U), float(eps), int(nsteps), sh))
+
+
+def mdwf_plaquette_dev(ctx, U):
+    p = _D()
+    _check(ctx, _lib.mdwf_plaquette_dev(ctx.handle, _gauge_dev(ctx, U), ctypes.byref(p)))
+    return p.value
+
+
+def flowed_gauge_dev(ctx, U_host, flow_t=1.0, flow_eps=0.01):
+    """Flow a host gauge field on the device to flow time flow_t; returns the host
+    result (numpy complex128, the layout mdwf_load_gauge takes)."""
+    import torch
+    U = torch.from_numpy(np.ascontiguousarray(U_host, dtype=np.complex128)).to('cuda')
+    mdwf_wilson_flow_dev(ctx, U, flow_eps, int(round(flow_t / flow_eps)))
+    return U.cpu().numpy()
 
 
 def mdwf_autotune(ctx, cfg_id, n, precision=MDWF_PREC_HALF, include_tensor_core=False):
