@@ -334,7 +334,7 @@ Tiling tiling_for(const Geom& g, int L5, int N, int nsb, bool two_buffers) {
 // Scalar kernels of the batched CG (one thread per RHS slot)
 // ---------------------------------------------------------------------------
 struct Scal {
-  double *gamma, *gamma_prev, *alpha, *beta, *rho2, *rho2_max, *stop2, *qq, *rr, *tmp, *bhat2;
+  double *gamma, *gamma_prev, *alpha, *beta, *rho2, *rho2_max, *stop2, *qq, *rr, *tmp, *bhat2, *upd2;
   int *active, *flags, *iters;
   double delta2;  // periodic reliable update when |rho|^2 < delta2 * max |rho|^2 since the last one
   double tau2;    // FP64 re-reference when |rho|^2 <= tau2 * |bhat|^2 (bhat = current reference residual)
@@ -365,20 +365,28 @@ __global__ void k_beta(Scal c, int N) {
     c.iters[r] += 1;
   }
 }
-// After a residual recomputed with FP32 arithmetic: its error is ~1e-7 |bhat|,
-// so it may declare convergence only once bhat itself is small (a re-reference
-// has happened); otherwise an FP64 re-reference is requested.
+// After a residual recomputed with FP32 arithmetic.  Its error grows like
+// 1e-7 kappa(Mhat) |bhat| (x_hi, accumulated since the last re-reference, is
+// about kappa times bhat), so for light quarks it can sit above any fixed
+// re-reference threshold.  An FP64 re-reference is requested when the residual
+// reached tau |bhat|, when it fell below the stopping norm (the FP64 residual
+// decides), or when it did not halve since the previous FP32 update (its
+// accuracy floor).  Convergence is accepted on the FP32 residual alone only
+// when bhat itself is within 10^3 of the stopping norm.
 __global__ void k_after_update(Scal c, int N, const int* um) {
   int r = threadIdx.x;
   if (r < N && um[r]) {
     double v = c.tmp[r];
+    const double prev = c.upd2[r];
     c.rho2[r] = v;
     c.rho2_max[r] = v;
+    c.upd2[r] = v;
     c.gamma[r] = c.rr[r];
     c.beta[r] = c.gamma_prev[r] > 0.0 ? c.gamma[r] / c.gamma_prev[r] : 0.0;
-    bool fine = c.bhat2[r] <= 1e11 * c.stop2[r];
+    const bool fine = c.bhat2[r] <= 1e6 * c.stop2[r];
+    const bool stalled = prev > 0.0 && v > 0.25 * prev;
     if (v <= c.stop2[r] && fine) { c.flags[r] = FLAG_DONE; c.active[r] = 0; }
-    else if (v <= c.stop2[r] || v <= c.tau2 * c.bhat2[r]) { c.flags[r] = FLAG_REREF; c.active[r] = 1; }
+    else if (v <= c.stop2[r] || v <= c.tau2 * c.bhat2[r] || stalled) { c.flags[r] = FLAG_REREF; c.active[r] = 1; }
     else { c.flags[r] = 0; c.active[r] = 1; }
   }
 }
@@ -390,6 +398,7 @@ __global__ void k_after_reref(Scal c, int N, const int* um) {
     c.rho2[r] = v;
     c.rho2_max[r] = v;
     c.bhat2[r] = v;
+    c.upd2[r] = 0.0;
     c.gamma[r] = c.rr[r];
     c.beta[r] = c.gamma_prev[r] > 0.0 ? c.gamma[r] / c.gamma_prev[r] : 0.0;
     if (v <= c.stop2[r]) { c.flags[r] = FLAG_DONE; c.active[r] = 0; }
@@ -591,6 +600,11 @@ struct BatchSolver {
   int* errw = nullptr;            // device status word of the bounded waits
   std::string wsp;                // prefix of this solver's workspace names (sessions own theirs)
   int tune_request = -1;          // HOP_AUTO / HOP_TUNE_ALL: pick the inner hop form by timing (tune())
+  // Sources b_e, b_o: own fields (sessions, whose sources arrive one at a time), or
+  // views of fields that are free when they are needed (the batch solve: rho64 and
+  // x_hi before the iterations, bhat and x_hi after them; repacked from the caller's
+  // sources, which stay valid for the whole call)
+  bool own_b = false;
 
   ~BatchSolver() { if (graph) cudaGraphExecDestroy(graph); }
 
@@ -633,27 +647,37 @@ struct BatchSolver {
     tune_request = (variant == HOP_AUTO || variant == HOP_TUNE_ALL) && nsb == 0 ? variant : -1;
     op64.launches = op32.launches = opS.launches = &launches;
     profiling = profile;
-    F<double>* f64[] = {&b_e, &b_o, &x_acc, &x_hi, &x_o, &bhat, &rho64, &u64, &t64};
-    const char* n64[] = {"b_e", "b_o", "x_acc", "x_hi", "x_o", "bhat", "rho64", "u64", "t64"};
-    for (int i = 0; i < 9; i++) CK(ws_field<double>(c, wsp + n64[i], units, f64[i]));
+    F<double>* f64[] = {&x_acc, &x_hi, &x_o, &bhat, &rho64, &u64, &t64};
+    const char* n64[] = {"x_acc", "x_hi", "x_o", "bhat", "rho64", "u64", "t64"};
+    for (int i = 0; i < 7; i++) CK(ws_field<double>(c, wsp + n64[i], units, f64[i]));
+    if (own_b) {
+      CK(ws_field<double>(c, wsp + "b_e", units, &b_e));
+      CK(ws_field<double>(c, wsp + "b_o", units, &b_o));
+    }
     if (!kFP64) {
-      F<float>* f32[] = {&xf, &uf, &tf, &qf};
-      const char* n32[] = {"xf", "uf", "tf", "qf"};
-      for (int i = 0; i < 4; i++) CK(ws_field<float>(c, wsp + n32[i], units, f32[i]));
+      // the FP32 reliable-update fields live in the FP64 temporaries u64 and t64:
+      // an update (update32) and a re-reference (reref) never overlap
+      const size_t n = 24 * (size_t)units;
+      xf.v = reinterpret_cast<float*>(u64.v);
+      uf.v = reinterpret_cast<float*>(u64.v) + n;
+      tf.v = reinterpret_cast<float*>(t64.v);
+      qf.v = reinterpret_cast<float*>(t64.v) + n;
+      xf.n = uf.n = tf.n = qf.n = nullptr;
     }
     F<S>* fS[] = {&p, &u, &t, &q, &rho, &r};
     const char* nS[] = {"p", "u", "t", "q", "rho", "r"};
     for (int i = 0; i < 6; i++) CK(ws_field<S>(c, wsp + "S." + nS[i], units, fS[i]));
     CK(ws_field<SX>(c, wsp + "xlo", units, &xlo));
     part = (double*)ws_get(c, wsp + "partials", sizeof(double) * g.Vh * N, &e); CK(e);
-    double* d = (double*)ws_get(c, wsp + "scal_d", sizeof(double) * 11 * N, &e); CK(e);
+    double* d = (double*)ws_get(c, wsp + "scal_d", sizeof(double) * 12 * N, &e); CK(e);
     int* ip = (int*)ws_get(c, wsp + "scal_i", sizeof(int) * 3 * N, &e); CK(e);
     umask_d = (int*)ws_get(c, wsp + "umask", sizeof(int) * N, &e); CK(e);
     sc.gamma = d; sc.gamma_prev = d + N; sc.alpha = d + 2 * N; sc.beta = d + 3 * N; sc.rho2 = d + 4 * N;
     sc.rho2_max = d + 5 * N; sc.stop2 = d + 6 * N; sc.qq = d + 7 * N; sc.rr = d + 8 * N; sc.tmp = d + 9 * N;
     sc.bhat2 = d + 10 * N;
+    sc.upd2 = d + 11 * N;
     sc.active = ip; sc.flags = ip + N; sc.iters = ip + 2 * N;
-    CK(cudaMemsetAsync(d, 0, sizeof(double) * 11 * N, st));
+    CK(cudaMemsetAsync(d, 0, sizeof(double) * 12 * N, st));
     CK(cudaMemsetAsync(ip, 0, sizeof(int) * 3 * N, st));
     const size_t b64 = sizeof(double) * 24 * (size_t)units;
     CK(cudaMemsetAsync(x_acc.v, 0, b64, st));
@@ -902,6 +926,8 @@ int solve_batch_impl(mdwf_ctx* ctx, Cfg* cfg, int n, const double* const* srcs, 
   const int N = n, L5 = cfg->act.L5;
   F<double> none;
   sv.launches += 2 * N;
+  sv.b_e = sv.rho64;
+  sv.b_o = sv.x_hi;
   for (int i = 0; i < N; i++) {
     CK(pack_rhs<double>(srcs[i], sv.b_e.v, nullptr, g, L5, N, 0, i, st));
     CK(pack_rhs<double>(srcs[i], sv.b_o.v, nullptr, g, L5, N, 1, i, st));
@@ -923,7 +949,7 @@ int solve_batch_impl(mdwf_ctx* ctx, Cfg* cfg, int n, const double* const* srcs, 
   }
   CK(cudaMemcpyAsync(sv.sc.stop2, stop2.data(), sizeof(double) * N, cudaMemcpyHostToDevice, st));
   sv.sc.delta2 = BatchSolver<S>::kFP64 ? 0.0 : o.delta * o.delta;
-  sv.sc.tau2 = BatchSolver<S>::kFP64 ? 0.0 : 1e-10;
+  sv.sc.tau2 = BatchSolver<S>::kFP64 ? 0.0 : 1e-6;
   // bhat_e = b_e + 1/2 H_eo B A^-1 b_o   (B A^-1 on the odd sites with the dense table kernel)
   {
     Op<double, double> loc;
@@ -937,6 +963,8 @@ int solve_batch_impl(mdwf_ctx* ctx, Cfg* cfg, int n, const double* const* srcs, 
     CK(loc.run(false, 1, 0, sv.b_o, none, M[MK_BAinv], none, nullptr, 0.0, sv.t64, nullptr, nullptr));
     CK(sv.op64.run(E_RAW, 0, 0, sv.t64, none, sv.b_e, 0.0, 0.5, sv.bhat, nullptr, nullptr));
   }
+  // x_hi held b_o: the solution starts from zero
+  CK(cudaMemsetAsync(sv.x_hi.v, 0, sizeof(double) * 24 * (size_t)g.Vh * L5 * N, st));
   // initial residual (x = 0)
   std::vector<int> um(N);
   for (int i = 0; i < N; i++) um[i] = act[i];
@@ -1011,6 +1039,14 @@ int solve_batch_impl(mdwf_ctx* ctx, Cfg* cfg, int n, const double* const* srcs, 
   sv.launches += 2 + 2 * N;
   CK(accum_xhi<typename BatchSolver<S>::SX>(sv.x_hi.v, sv.xlo.v, sv.tl_blas, g.Vh, L5, N, nullptr, st));
   CK(accum_xhi<double>(sv.x_acc.v, sv.x_hi.v, sv.tl_blas, g.Vh, L5, N, nullptr, st));
+  // sources again, in fields now free (bhat, x_hi)
+  sv.b_e = sv.bhat;
+  sv.b_o = sv.x_hi;
+  sv.launches += 2 * N;
+  for (int i = 0; i < N; i++) {
+    CK(pack_rhs<double>(srcs[i], sv.b_e.v, nullptr, g, L5, N, 0, i, st));
+    CK(pack_rhs<double>(srcs[i], sv.b_o.v, nullptr, g, L5, N, 1, i, st));
+  }
   // x_o = A^-1 (b_o + 1/2 H_oe B x_e)
   sv.launches += 2;
   CK(bop<double>(sv.x_acc.v, nullptr, sv.u64.v, nullptr, sv.op64.f, sv.tl_blas, g.Vh, L5, N, nullptr, st));
@@ -1121,10 +1157,11 @@ struct SessionImpl : SessionBase {
     b2.assign(N, 0.0);
     t0.resize(N);
     sv.wsp = prefix;
+    sv.own_b = true;
     int rc = sv.init(c, cf, masses, o.nsb, o.profile != 0, o, s);
     if (rc) return rc;
     sv.sc.delta2 = BatchSolver<S>::kFP64 ? 0.0 : o.delta * o.delta;
-    sv.sc.tau2 = BatchSolver<S>::kFP64 ? 0.0 : 1e-10;
+    sv.sc.tau2 = BatchSolver<S>::kFP64 ? 0.0 : 1e-6;
     cudaError_t e = cudaSuccess;
     fmask = (int*)ws_get(c, prefix + "fmask", sizeof(int) * N, &e);
     CK(e);
@@ -1163,7 +1200,7 @@ struct SessionImpl : SessionBase {
     int* ia[] = {sv.sc.active, sv.sc.flags, sv.sc.iters};
     for (int* a : ia) CK(cudaMemcpyAsync(a + r, &zi, sizeof(int), cudaMemcpyHostToDevice, st));
     double* da[] = {sv.sc.gamma, sv.sc.gamma_prev, sv.sc.alpha, sv.sc.beta, sv.sc.rho2, sv.sc.rho2_max, sv.sc.qq,
-                    sv.sc.rr, sv.sc.tmp, sv.sc.bhat2};
+                    sv.sc.rr, sv.sc.tmp, sv.sc.bhat2, sv.sc.upd2};
     for (double* a : da)
       CK(cudaMemcpyAsync(a + r, &zd, sizeof(double), cudaMemcpyHostToDevice, st));
     const int* m = sv.umask_d;
@@ -1785,9 +1822,9 @@ long long mdwf_session_bytes(mdwf_ctx* ctx, int cfg_id, int slots, int precision
   const double s = precision == MDWF_PREC_DOUBLE ? 192 : precision == MDWF_PREC_SINGLE ? 96
                  : precision == MDWF_PREC_HALF ? 52 : 48;
   const double x = precision == MDWF_PREC_DOUBLE ? 192 : 96;
-  const double f32 = precision == MDWF_PREC_DOUBLE ? 0 : 4 * 96;
-  // nine FP64 fields, the FP32 update fields, six inner fields, x_lo, partial sums
-  return (long long)(units * (9 * 192 + f32 + 6 * s + x) + (double)ctx->g.Vh * slots * 8 + 4096.0 * slots);
+  // nine FP64 fields (seven solver fields and the slots' own sources; the FP32
+  // update fields share two of them), six inner fields, x_lo, partial sums
+  return (long long)(units * (9 * 192 + 6 * s + x) + (double)ctx->g.Vh * slots * 8 + 4096.0 * slots);
 }
 
 int mdwf_session_create(mdwf_ctx* ctx, int cfg_id, int slots, const mdwf_solver_opts* opts, double tol, void* stream,

@@ -414,3 +414,18 @@ def test_planted_mistakes():
     }
     for name, over in planted.items():
         assert not _pins_pass(_Patched(**over)), "planted mistake not caught: " + name
+
+
+def test_sampled_site_operator_equals_full_operator():
+    """The single-site D x used for sampled checks of full-size results equals the
+    full-lattice D x at those sites (every boundary case of the window)."""
+    import sampled
+    dims, L5 = (4, 3, 2, 5), 4
+    U = synth.random_gauge(dims, 21, 0.6)
+    x = synth.gaussian_spinor((L5, 5, 2, 3, 4, 4, 3), 22)
+    act = (1.3, 1.5, 0.5, 0.07)
+    full = O.mobius(U, x, *act)
+    for site in [(0, 0, 0, 0), (3, 2, 1, 4), (1, 1, 0, 2), (2, 0, 1, 0), (0, 2, 1, 4)]:
+        got = sampled.dx_at_site(U, x, site, *act)
+        xs, ys, zs, ts = site
+        assert np.abs(got - full[:, ts, zs, ys, xs]).max() < 1e-13
