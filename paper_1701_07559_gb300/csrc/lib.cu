@@ -199,18 +199,23 @@ struct Tables {
 template <typename T>
 struct DevTables {
   DBuf buf;
+  T* ext = nullptr;     // a buffer of the context's workspace instead of buf (no allocation per call)
   size_t blk = 0;
-  cudaError_t upload(const Tables& t, cudaStream_t st) {
+  cudaError_t upload(const Tables& t, cudaStream_t st, T* into = nullptr) {
     blk = t.block();
     std::vector<T> v(t.h.size());
     for (size_t i = 0; i < v.size(); i++) v[i] = (T)t.h[i];
-    cudaError_t e = buf.alloc(sizeof(T) * v.size());
-    if (e != cudaSuccess) return e;
-    e = cudaMemcpyAsync(buf.p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, st);
+    ext = into;
+    if (!ext) {
+      cudaError_t e = buf.alloc(sizeof(T) * v.size());
+      if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = cudaMemcpyAsync(base(), v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return e;
     return cudaStreamSynchronize(st);
   }
-  const T* operator[](int k) const { return buf.as<T>() + (size_t)k * blk; }
+  T* base() const { return ext ? ext : buf.as<T>(); }
+  const T* operator[](int k) const { return base() + (size_t)k * blk; }
 };
 
 // ---------------------------------------------------------------------------
@@ -553,6 +558,16 @@ void* ws_get(mdwf_ctx* ctx, const std::string& name, size_t bytes, cudaError_t* 
     e.second = bytes;
   }
   return e.first;
+}
+
+// Tables uploaded into a named workspace buffer of the context (no allocation once it exists).
+template <typename T>
+cudaError_t upload_tables_ws(mdwf_ctx* ctx, const std::string& name, const Tables& t, DevTables<T>* M,
+                             cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
+  T* p = (T*)ws_get(ctx, name, sizeof(T) * t.h.size(), &e);
+  if (e != cudaSuccess) return e;
+  return M->upload(t, st, p);
 }
 
 template <typename S>
@@ -959,7 +974,7 @@ int solve_batch_impl(mdwf_ctx* ctx, Cfg* cfg, int n, const double* const* srcs, 
     Tables tab;
     tab.build(cfg->act, masses);
     DevTables<double> M;
-    CK(M.upload(tab, st));
+    CK(upload_tables_ws<double>(ctx, sv.wsp + "tables", tab, &M, st));
     CK(loc.run(false, 1, 0, sv.b_o, none, M[MK_BAinv], none, nullptr, 0.0, sv.t64, nullptr, nullptr));
     CK(sv.op64.run(E_RAW, 0, 0, sv.t64, none, sv.b_e, 0.0, 0.5, sv.bhat, nullptr, nullptr));
   }
@@ -1229,7 +1244,7 @@ struct SessionImpl : SessionBase {
       Tables tab;
       tab.build(cfg->act, masses);
       DevTables<double> M;
-      CK(M.upload(tab, st));
+      CK(upload_tables_ws<double>(ctx, sv.wsp + "tables", tab, &M, st));
       CK(loc.run(false, 1, 0, sv.b_o, none, M[MK_BAinv], none, nullptr, 0.0, sv.t64, m, nullptr));
       CK(sv.op64.run(E_RAW, 0, 0, sv.t64, none, sv.b_e, 0.0, 0.5, sv.bhat, m, nullptr));
     }
@@ -1390,21 +1405,29 @@ int apply_dev(mdwf_ctx* ctx, Cfg* cfg, int kind, int arg1, int arg2, const doubl
   Tables tab;
   tab.build(cfg->act, std::vector<double>(1, cfg->act.mf));
   DevTables<double> M;
-  CK(M.upload(tab, st));
+  CK(upload_tables_ws<double>(ctx, "apply.tables", tab, &M, st));
   long units = g.Vh * L5;
-  FieldBuf<double> ie, io, oe, oo, te, to;
-  for (auto* f : {&ie, &io, &oe, &oo, &te, &to}) CK(f->alloc(units));
-  CK(pack_rhs<double>(in_dev, ie.v.as<double>(), nullptr, g, L5, 1, 0, 0, st));
-  CK(pack_rhs<double>(in_dev, io.v.as<double>(), nullptr, g, L5, 1, 1, 0, st));
-  CK(cudaMemsetAsync(oe.v.p, 0, oe.v.bytes, st));
-  CK(cudaMemsetAsync(oo.v.p, 0, oo.v.bytes, st));
+  // fields of the context's workspace: no allocation (and no device-wide
+  // synchronisation of a free) once they exist
+  struct WF {
+    F<double> w;
+    F<double> f() const { return w; }
+  } ie, io, oe, oo, te, to;
+  const char* names[] = {"apply.ie", "apply.io", "apply.oe", "apply.oo", "apply.te", "apply.to"};
+  WF* fs[] = {&ie, &io, &oe, &oo, &te, &to};
+  for (int i = 0; i < 6; i++) CK(ws_field<double>(ctx, names[i], units, &fs[i]->w));
+  CK(pack_rhs<double>(in_dev, ie.w.v, nullptr, g, L5, 1, 0, 0, st));
+  CK(pack_rhs<double>(in_dev, io.w.v, nullptr, g, L5, 1, 1, 0, st));
+  CK(cudaMemsetAsync(oe.w.v, 0, sizeof(double) * 24 * (size_t)units, st));
+  CK(cudaMemsetAsync(oo.w.v, 0, sizeof(double) * 24 * (size_t)units, st));
   F<double> none;
-  DBuf mass;
-  CK(mass.alloc(sizeof(double)));
-  CK(cudaMemcpyAsync(mass.p, &cfg->act.mf, sizeof(double), cudaMemcpyHostToDevice, st));
+  cudaError_t me = cudaSuccess;
+  double* mass = (double*)ws_get(ctx, "apply.mass", sizeof(double), &me);
+  CK(me);
+  CK(cudaMemcpyAsync(mass, &cfg->act.mf, sizeof(double), cudaMemcpyHostToDevice, st));
   FastOp<double, double> fo;
   fo.g = g; fo.L5 = L5; fo.N = 1; fo.anti = cfg->anti; fo.U = cfg->U64; fo.st = st;
-  fo.f = make_fifth<double>(cfg->act, mass.as<double>());
+  fo.f = make_fifth<double>(cfg->act, mass);
   choose_hop(fo, cfg, 0, HOP_DIRECT, nullptr);
   Tiling tb = make_tiling(g.Vh, L5, 1, 2, 512);
   if (kind == 0) {
@@ -1434,12 +1457,12 @@ int apply_dev(mdwf_ctx* ctx, Cfg* cfg, int kind, int arg1, int arg2, const doubl
     const double f = 1.0 - cfg->act.c5 * (4.0 - cfg->act.M5);
     for (int chi = 0; chi < 2; chi++) for (int s = 0; s < L5; s++) sc.h[((size_t)chi * L5 + s) * L5 + s] = f;
     DevTables<double> G;
-    CK(G.upload(sc, st));
+    CK(upload_tables_ws<double>(ctx, "apply.stables", sc, &G, st));
     CK(op.run(true, 0, 0, io.f(), ie.f(), G[0], none, nullptr, 0.5 * cfg->act.c5, oe.f(), nullptr, nullptr));
     CK(op.run(true, 1, 0, ie.f(), io.f(), G[0], none, nullptr, 0.5 * cfg->act.c5, oo.f(), nullptr, nullptr));
   }
-  CK(unpack_rhs<double>(oe.v.as<double>(), nullptr, out_dev, g, L5, 1, 0, 0, st));
-  CK(unpack_rhs<double>(oo.v.as<double>(), nullptr, out_dev, g, L5, 1, 1, 0, st));
+  CK(unpack_rhs<double>(oe.w.v, nullptr, out_dev, g, L5, 1, 0, 0, st));
+  CK(unpack_rhs<double>(oo.w.v, nullptr, out_dev, g, L5, 1, 1, 0, st));
   CK(cudaStreamSynchronize(st));
   return MDWF_OK;
 }

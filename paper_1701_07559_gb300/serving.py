@@ -9,12 +9,15 @@ Each configuration has its own library context (its gauge links stay resident
 in HBM), its own CUDA stream and, while it has work, one solver session: a
 fixed number of slots whose CG state lives on the device.  Requests wait in a
 queue and are admitted into free slots between CG chunks; converged slots are
-finalised and freed at the next poll.  Sessions of different configurations
-are driven on their own streams, so their chunks overlap on the device.
+finalised and freed at the next poll.  Each configuration's session is driven
+by a host thread of its own on its own stream, so sessions progress at their own
+pace and their chunks overlap on the device (the library calls release the
+Python interpreter lock).
 
 Admission is by HBM footprint: a session is created only when its device bytes
 (as the library reports them), plus the solution fields of its slots, fit in
-the budget beside the gauge fields and the other sessions.  When a
+the budget beside the gauge fields and the other sessions; its slot count is
+capped at a fair share of the budget per resident configuration.  When a
 configuration cannot get a session, the others stop taking new requests until
 one of them is idle and can be released (so no configuration starves).
 
@@ -23,6 +26,7 @@ tensors through PyTorch and keeps the clock.
 """
 import collections
 import dataclasses
+import threading
 import time
 
 import numpy as np
@@ -120,6 +124,7 @@ class Server:
         self.blocked = None          # name of a configuration waiting for room
         self.samples = []            # (time, queued, running, bytes in use)
         self.done = []
+        self.cv = threading.Condition(threading.RLock())
 
     # --- configurations -------------------------------------------------------
     def add_config(self, name, dims, U, M5, b5, c5, mf, L5, t_antiperiodic=1):
@@ -129,9 +134,23 @@ class Server:
         L.mdwf_load_gauge(ctx, 0, U, t_antiperiodic)
         L.mdwf_set_action(ctx, 0, M5, b5, c5, mf, L5)
         V = int(np.prod(dims))
-        gauge_bytes = V * 4 * (144 + 80 + 36)   # FP64, padded FP32 and fp16 link copies
-        stream = self.torch.cuda.Stream(self.dev) if self.on_gpu else None
-        self.configs[name] = _Config(name, ctx, dims, int(L5), stream, gauge_bytes)
+        # FP64, padded FP32 and fp16-fragment link copies, and the library's workspace
+        # of six FP64 half-lattice fields for the device source construction
+        gauge_bytes = V * 4 * (144 + 80 + 256) + 3 * int(L5) * V * 12 * 16
+        self.configs[name] = _Config(name, ctx, dims, int(L5), None, gauge_bytes)
+        self._prioritise()
+
+    def _prioritise(self):
+        """Give every configuration a stream whose priority ranks it by the cost of
+        one request (smallest lattice first): the device then schedules the
+        blocks of cheap requests ahead of queued blocks of expensive ones
+        (shortest job first), which bounds their latency under a mixed load."""
+        if not self.on_gpu:
+            return
+        order = sorted(self.configs.values(), key=lambda c: c.field_bytes)
+        for rank, c in enumerate(order):
+            if c.session is None:
+                c.stream = self.torch.cuda.Stream(self.dev, priority=-(len(order) - 1 - rank))
 
     def close(self):
         for c in self.configs.values():
@@ -169,9 +188,13 @@ class Server:
             if self.on_gpu:
                 self.torch.cuda.empty_cache()
             free = self.budget - self.bytes_in_use()
+        # at most a fair share of the budget per resident configuration (at least one slot)
+        share = (self.budget - sum(o.gauge_bytes for o in self.configs.values())) // max(1, len(self.configs))
         slots = self.max_slots
-        while slots > 0 and self._slot_bytes(c, slots) > free:
+        while slots > 1 and self._slot_bytes(c, slots) > min(free, share):
             slots -= 1
+        if self._slot_bytes(c, slots) > free:
+            slots = 0
         if slots == 0:
             if not any(o.session is not None or o.running for o in self.configs.values() if o is not c):
                 raise MemoryError('configuration %r does not fit in the HBM budget (%d bytes)' % (c.name, self.budget))
@@ -214,83 +237,138 @@ class Server:
             raise ValueError('unknown source kind %r' % (kind,))
         L.mdwf_make_source_dev(c.ctx, 0, c.eta, c.src, stream=c.stream)
 
+    def _admit_config(self, c, now):
+        """Admit queued requests of configuration c into free slots (lock held)."""
+        if not c.queue or (self.blocked is not None and self.blocked != c.name):
+            return
+        if c.session is None:
+            if not self._open_session(c):
+                if self.blocked is None:
+                    self.blocked = c.name
+                return
+            if self.blocked == c.name:
+                self.blocked = None
+        while c.queue and len(c.running) < c.slots:
+            if self.bytes_in_use() + c.field_bytes > self.budget:
+                break
+            req = c.queue.popleft()
+            x = self.torch.empty(c.shape5, dtype=self.torch.complex128, device=self.dev)
+            self._source(c, req)
+            self.lib.mdwf_session_submit(c.session, c.src, req.mass, x, req.tag)
+            req.t_admit = now
+            req.x = x
+            c.running[req.tag] = req
+
     def _admit(self):
         now = self.clock()
         order = sorted((c for c in self.configs.values() if c.queue), key=lambda c: c.queue[0].t_arrival)
         for c in order:
-            if self.blocked is not None and self.blocked != c.name:
-                continue
-            if c.session is None:
-                if not self._open_session(c):
-                    if self.blocked is None:
-                        self.blocked = c.name
-                    continue
-                if self.blocked == c.name:
-                    self.blocked = None
-            while c.queue and len(c.running) < c.slots:
-                if self.bytes_in_use() + c.field_bytes > self.budget:
-                    break
-                req = c.queue.popleft()
-                x = self.torch.empty(c.shape5, dtype=self.torch.complex128, device=self.dev)
-                self._source(c, req)
-                self.lib.mdwf_session_submit(c.session, c.src, req.mass, x, req.tag)
-                req.t_admit = now
-                req.x = x
-                c.running[req.tag] = req
+            self._admit_config(c, now)
+
+    def _collect(self, c, done):
+        out = []
+        for tag, st in done:
+            req = c.running.pop(tag)
+            req.t_done = self.clock()
+            req.stats = st
+            if not self.keep:
+                req.x = None
+            out.append(req)
+        self.done.extend(out)
+        self.samples.append((self.clock(), sum(len(o.queue) for o in self.configs.values()),
+                             sum(len(o.running) for o in self.configs.values()), self.bytes_in_use()))
+        return out
 
     def step(self):
-        """Admit what fits, run one CG chunk on every busy session (overlapping on
-        their streams), then collect completed requests.  Returns them."""
-        self._admit()
-        busy = [c for c in self.configs.values() if c.running]
+        """Single-threaded driving: admit what fits, run one CG chunk on every busy
+        session, then collect completed requests.  Returns them."""
+        with self.cv:
+            self._admit()
+            busy = [c for c in self.configs.values() if c.running]
         for c in busy:
             self.lib.mdwf_session_launch(c.session)
         out = []
         for c in busy:
-            for tag, st in self.lib.mdwf_session_poll(c.session):
-                req = c.running.pop(tag)
-                req.t_done = self.clock()
-                req.stats = st
-                if not self.keep:
-                    req.x = None
-                out.append(req)
-        for c in self.configs.values():
-            if c.session is not None and not c.running and self.blocked not in (None, c.name):
-                self._release(c)
-        self.samples.append((self.clock(), sum(len(c.queue) for c in self.configs.values()),
-                             sum(len(c.running) for c in self.configs.values()), self.bytes_in_use()))
-        self.done.extend(out)
+            done = self.lib.mdwf_session_poll(c.session)
+            with self.cv:
+                out.extend(self._collect(c, done))
+        with self.cv:
+            for c in self.configs.values():
+                if c.session is not None and not c.running and self.blocked not in (None, c.name):
+                    self._release(c)
         return out
+
+    def _worker(self, c, stop, errors):
+        """Drive configuration c's session until stop is set and c has no work."""
+        try:
+            while True:
+                with self.cv:
+                    if stop.is_set() and not c.queue and not c.running:
+                        return
+                    self._admit_config(c, self.clock())
+                    if not c.running:
+                        if c.session is not None and self.blocked not in (None, c.name):
+                            self._release(c)
+                            self.cv.notify_all()
+                        self.cv.wait(timeout=0.01)
+                        continue
+                    sess = c.session
+                self.lib.mdwf_session_launch(sess)
+                done = self.lib.mdwf_session_poll(sess)
+                with self.cv:
+                    self._collect(c, done)
+                    self.cv.notify_all()
+        except BaseException as e:      # reported by run()
+            errors.append(e)
+            stop.set()
+            with self.cv:
+                self.cv.notify_all()
 
     def idle(self):
         return not any(c.queue or c.running for c in self.configs.values())
 
     def run(self, requests, arrivals=None, deadline=None):
         """Serve `requests` arriving at the given times (seconds after the start;
-        None: all at once) and return them completed, in completion order."""
+        None: all at once), one driving thread per configuration.  Returns them
+        completed, in completion order."""
         pending = list(requests)
         if arrivals is None:
             arrivals = np.zeros(len(pending))
         order = np.argsort(arrivals, kind='stable')
         pending = [pending[i] for i in order]
         times = [float(arrivals[i]) for i in order]
+        n0 = len(self.done)
+        stop, errors = threading.Event(), []
+        workers = [threading.Thread(target=self._worker, args=(c, stop, errors), daemon=True)
+                   for c in self.configs.values()]
         t0 = self.clock()
-        k = 0
-        finished = []
-        while k < len(pending) or not self.idle():
-            now = self.clock() - t0
-            while k < len(pending) and times[k] <= now:
-                pending[k].t_arrival = t0 + times[k]
-                self.submit(pending[k])
-                k += 1
-            if self.idle():
-                if k < len(pending):
-                    time.sleep(max(0.0, min(0.05, times[k] - now)))
-                continue
-            finished.extend(self.step())
-            if deadline is not None and self.clock() - t0 > deadline:
-                raise TimeoutError('serving run exceeded its deadline')
-        return finished
+        for w in workers:
+            w.start()
+        try:
+            for req, t in zip(pending, times):
+                while not errors:
+                    wait = t - (self.clock() - t0)
+                    if wait <= 0:
+                        break
+                    time.sleep(min(wait, 0.05))
+                if errors:
+                    break
+                with self.cv:
+                    req.t_arrival = t0 + t
+                    self.submit(req)
+                    self.cv.notify_all()
+        finally:
+            stop.set()
+            with self.cv:
+                self.cv.notify_all()
+            for w in workers:
+                left = None if deadline is None else max(0.0, deadline - (self.clock() - t0))
+                w.join(left)
+        if errors:
+            raise errors[0]
+        if any(w.is_alive() for w in workers):
+            raise TimeoutError('serving run exceeded its deadline')
+        return self.done[n0:]
 
     @staticmethod
     def metrics(reqs):
