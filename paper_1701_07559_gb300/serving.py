@@ -303,7 +303,7 @@ class Server:
         try:
             while True:
                 with self.cv:
-                    if stop.is_set() and not c.queue and not c.running:
+                    if errors or (stop.is_set() and not c.queue and not c.running):
                         return
                     self._admit_config(c, self.clock())
                     if not c.running:

@@ -127,17 +127,18 @@ def test_admission_by_memory_and_no_starvation(serving):
     field = lambda dims, L5: L5 * int(np.prod(dims)) * 12 * 16
     slot = {fa: 10 ** 6, fb: 10 ** 6}
     fake = FakeLib(slot)
-    gauge = lambda dims: int(np.prod(dims)) * 4 * (144 + 80 + 36)
-    budget = gauge(fa) + gauge(fb) + 10 ** 6 + 3 * field(fb, 4) + field(fb, 4) + 10 ** 5
-    srv = _server(serving, fake, budget=budget, max_slots=1)
+    srv = _server(serving, fake, budget=10 ** 12, max_slots=1)
     _add(srv, 'a', fa)
     _add(srv, 'b', fb)
+    gauges = sum(c.gauge_bytes for c in srv.configs.values())
+    # room for one session (with its scratch and one solution field) at a time
+    srv.budget = gauges + 10 ** 6 + 3 * field(fb, 4) + field(fb, 4) + 10 ** 5
     reqs = [serving.Request('a' if i % 2 == 0 else 'b', 0.03, ('z2', i)) for i in range(8)]
     done = srv.run(reqs)
     assert len(done) == 8
     assert fake.max_live == 1                          # never both sessions at once
     assert len(fake.created) >= 2 and {d for d, _ in fake.created} == {fa, fb}
-    assert srv.samples and max(s[3] for s in srv.samples) <= budget
+    assert srv.samples and max(s[3] for s in srv.samples) <= srv.budget
 
 
 def test_configuration_too_large_for_budget(serving):
