@@ -539,8 +539,7 @@ __device__ __forceinline__ int nbr_half_any(const Geom& g, const Site& x, int d)
 }
 
 // Shared memory of the direct kernel: the epilogue tile (threads x kPadF reals,
-// at least threads doubles), then per (site, direction) the neighbour half-site
-// index with the time-boundary flag in bit 31.
+// at least threads doubles).
 template <typename T>
 __host__ __device__ __forceinline__ size_t direct_tile_bytes(int threads) {
   size_t b = (size_t)threads * kPadF * sizeof(T);
@@ -552,33 +551,19 @@ template <typename S, typename T, int EPI>
 __global__ void hop_fast_kernel(FastArgs<S, T> a, Tiling tl) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const Thr t = thread_of(a, tl);
-  int* sNb = reinterpret_cast<int*>(smem_raw + direct_tile_bytes<T>(tl.threads));
-  const long h0 = (long)blockIdx.x * tl.nsb;
-  for (int k = t.tid; k < 8 * tl.nsb; k += tl.threads) {
-    const int j = k >> 3, d = k & 7;
-    int v = 0;
-    if (h0 + j < a.g.Vh) {
-      const Site x = make_site(a.g, a.out_par, h0 + j);
-      v = nbr_half_any(a.g, x, d);
-      if (a.antiperiodic && ((d == 6 && x.c[3] == a.g.L[3] - 1) || (d == 7 && x.c[3] == 0))) v |= (int)0x80000000u;
-    }
-    sNb[k] = v;
-  }
-  __syncthreads();
   T acc[24];
 #pragma unroll
   for (int i = 0; i < 24; i++) acc[i] = 0;
   if (t.act) {
-    const int* nb = sNb + 8 * t.site_l;
-    hop_term_at<0, true, S, T>(a, nb[0], false, t.h, t.s, t.r, nullptr, 1.f, acc);
-    hop_term_at<0, false, S, T>(a, nb[1], false, t.h, t.s, t.r, nullptr, 1.f, acc);
-    hop_term_at<1, true, S, T>(a, nb[2], false, t.h, t.s, t.r, nullptr, 1.f, acc);
-    hop_term_at<1, false, S, T>(a, nb[3], false, t.h, t.s, t.r, nullptr, 1.f, acc);
-    hop_term_at<2, true, S, T>(a, nb[4], false, t.h, t.s, t.r, nullptr, 1.f, acc);
-    hop_term_at<2, false, S, T>(a, nb[5], false, t.h, t.s, t.r, nullptr, 1.f, acc);
-    const int n6 = nb[6], n7 = nb[7];
-    hop_term_at<3, true, S, T>(a, n6 & 0x7fffffff, n6 < 0, t.h, t.s, t.r, nullptr, 1.f, acc);
-    hop_term_at<3, false, S, T>(a, n7 & 0x7fffffff, n7 < 0, t.h, t.s, t.r, nullptr, 1.f, acc);
+    const Site x = make_site(a.g, a.out_par, t.h);
+    hop_term<0, true, S, T>(a, x, t.h, t.s, t.r, nullptr, 1.f, acc);
+    hop_term<0, false, S, T>(a, x, t.h, t.s, t.r, nullptr, 1.f, acc);
+    hop_term<1, true, S, T>(a, x, t.h, t.s, t.r, nullptr, 1.f, acc);
+    hop_term<1, false, S, T>(a, x, t.h, t.s, t.r, nullptr, 1.f, acc);
+    hop_term<2, true, S, T>(a, x, t.h, t.s, t.r, nullptr, 1.f, acc);
+    hop_term<2, false, S, T>(a, x, t.h, t.s, t.r, nullptr, 1.f, acc);
+    hop_term<3, true, S, T>(a, x, t.h, t.s, t.r, nullptr, 1.f, acc);
+    hop_term<3, false, S, T>(a, x, t.h, t.s, t.r, nullptr, 1.f, acc);
   }
   epilogue<S, T, EPI>(a, tl, t, acc, reinterpret_cast<T*>(smem_raw));
 }
@@ -723,7 +708,7 @@ cudaError_t launch_one(const FastArgs<S, T>& a, const Tiling& t, cudaStream_t st
     hop_staged_kernel<S, T, EPI><<<grid, block, smem, st>>>(a, t, si);
     return cudaGetLastError();
   }
-  const size_t smem = direct_tile_bytes<T>(t.threads) + (size_t)t.nsb * 8 * sizeof(int);
+  const size_t smem = direct_tile_bytes<T>(t.threads);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(hop_fast_kernel<S, T, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
@@ -1135,6 +1120,161 @@ cudaError_t launch_mma_bulk_one(const FastArgs<__half, float>& a, const Tiling& 
   return cudaGetLastError();
 }
 
+// Tensor-core hop, thread-per-unit form.  Threads load and project their own
+// unit as the CUDA-core hop does (three 16-byte words per neighbour: the fastest
+// gather), write the projected half spinors (fp16) and the neighbour's scale to
+// a per-warp buffer in shared memory, and the warp reads them back in mma
+// fragment order: one m16n8k8 per 8-unit tile (rows = the two projected halves
+// of a unit, B = the link fragment of the tile's site), reconstructed in FP32
+// with the unit's scale by the lane that holds colour c of unit g.  Needs whole
+// warps and 8-unit tiles inside one site (L5 rt a multiple of 8).
+constexpr int kTpuWords = 32 * 4;                    // per warp: 32 units x (3 colour pairs + scale), 8-byte words
+
+template <int MU>
+__device__ __forceinline__ void project_pairs(const uint4 q[3], bool neg_sg, uint2* out) {
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    uint32_t h0, h1;
+    mma_project<MU>(q[c], neg_sg, h0, h1);
+    out[c] = make_uint2(h0, h1);
+  }
+}
+
+template <int MU, bool FWD>
+__device__ __forceinline__ void tpu_term(const FastArgs<__half, float>& a, const uint32_t* __restrict__ frag,
+                                         const int* nbw, int hn, bool bflip, bool act, long un, uint2* wb, int lane,
+                                         int g, int c, bool dag, long lf_or_base, float* acc) {
+  // 1. own unit: load, project, publish
+  uint4 q[3] = {make_uint4(0u, 0u, 0u, 0u), make_uint4(0u, 0u, 0u, 0u), make_uint4(0u, 0u, 0u, 0u)};
+  float sc = 0.f;
+  if (act) {
+    const uint4* p = reinterpret_cast<const uint4*>(a.in) + un * 3;
+    q[0] = __ldg(p);
+    q[1] = __ldg(p + 1);
+    q[2] = __ldg(p + 2);
+    sc = __ldg(a.in_nrm + un);
+  }
+  const bool neg_sg = FWD ? !dag : dag;
+  uint2 pr[3];
+  project_pairs<MU>(q, neg_sg, pr);
+  __syncwarp();
+  wb[lane * 4 + 0] = pr[0];
+  wb[lane * 4 + 1] = pr[1];
+  wb[lane * 4 + 2] = pr[2];
+  reinterpret_cast<float*>(wb + lane * 4 + 3)[0] = bflip ? -sc : sc;
+  __syncwarp();
+  // 2. four 8-unit tiles: lane (g, c) holds colour c of unit 8 t + g
+#pragma unroll
+  for (int t = 0; t < 4; t++) {
+    const int u = 8 * t + g;
+    const uint2 hv = c < 3 ? wb[u * 4 + c] : make_uint2(0u, 0u);
+    const float f = reinterpret_cast<const float*>(wb + u * 4 + 3)[0] * a.kappa;
+    // link of the tile's site: forward U_mu(x), backward U_mu(x - mu)^+ (nbw: the tile's site neighbour)
+    const long link = (lf_or_base + nbw[t]) * 4 + MU;
+    const uint32_t b = __ldg(frag + (link * 2 + (FWD ? 0 : 1)) * 32 + lane);
+    float d[4] = {0.f, 0.f, 0.f, 0.f};
+    mma_m16n8k8(hv.x, hv.y, b, d);
+    mma_reconstruct<MU>(d, f, neg_sg ? -f : f, acc + 8 * t);
+  }
+}
+
+template <int EPI>
+__global__ void hop_tpu_kernel(FastArgs<__half, float> a, Tiling tl, const uint32_t* __restrict__ frag) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* sA = reinterpret_cast<float*>(smem_raw);
+  const Thr t = thread_of(a, tl);
+  const int nthr = tl.threads;
+  size_t base = (size_t)nthr * kPadF * sizeof(float);
+  if (base < (size_t)nthr * sizeof(double)) base = (size_t)nthr * sizeof(double);
+  int* sNb = reinterpret_cast<int*>(smem_raw + base);                          // [nsb][8] (bit 31: boundary)
+  uint2* sW = reinterpret_cast<uint2*>(smem_raw + base + (((size_t)tl.nsb * 8 * sizeof(int) + 15) & ~(size_t)15));
+  const long h0 = (long)blockIdx.x * tl.nsb;
+  for (int k = t.tid; k < 8 * tl.nsb; k += nthr) {
+    const int j = k >> 3, d = k & 7;
+    int v = 0;
+    if (h0 + j < a.g.Vh) {
+      const Site x = make_site(a.g, a.out_par, h0 + j);
+      v = nbr_half_any(a.g, x, d);
+      if (a.antiperiodic && ((d == 6 && x.c[3] == a.g.L[3] - 1) || (d == 7 && x.c[3] == 0))) v |= (int)0x80000000u;
+    }
+    sNb[k] = v;
+  }
+  __syncthreads();
+  const int lane = t.tid & 31, warp = t.tid >> 5;
+  const int g = lane >> 2, c = lane & 3;
+  uint2* wb = sW + (size_t)warp * kTpuWords;
+  const bool dag = a.dagger != 0;
+  const int upb = a.L5 * tl.rt;
+  // the site (block-local) of each of the warp's four tiles, and of this thread's unit
+  int tsite[4];
+#pragma unroll
+  for (int q = 0; q < 4; q++) tsite[q] = (warp * 32 + 8 * q) / upb;
+  const int* nb = sNb + 8 * t.site_l;
+  const long un_base = (long)t.s * a.N + t.r;
+  const long upm = (long)a.L5 * a.N;
+  const bool act = t.act;
+  float acc[32];
+#pragma unroll
+  for (int i = 0; i < 32; i++) acc[i] = 0.f;
+  const long pf = (long)a.out_par * a.g.Vh + h0;           // forward links: site h0 + tsite
+  const long pb = (long)(1 - a.out_par) * a.g.Vh;          // backward links: neighbour site
+#define MDWF_TPU_DIR(D, MUV, FWDV)                                                                              \
+  {                                                                                                             \
+    const int raw = nb[D];                                                                                      \
+    const int hn = raw & 0x7fffffff;                                                                           \
+    int nbw[4];                                                                                                 \
+    _Pragma("unroll") for (int q = 0; q < 4; q++)                                                              \
+        nbw[q] = FWDV ? (h0 + tsite[q] < a.g.Vh ? tsite[q] : 0) : (sNb[8 * tsite[q] + D] & 0x7fffffff);           \
+    tpu_term<MUV, FWDV>(a, frag, nbw, hn, raw < 0, act, (long)hn * upm + un_base, wb, lane, g, c, dag,            \
+                        FWDV ? pf : pb, acc);                                                                    \
+  }
+  MDWF_TPU_DIR(0, 0, true)
+  MDWF_TPU_DIR(1, 0, false)
+  MDWF_TPU_DIR(2, 1, true)
+  MDWF_TPU_DIR(3, 1, false)
+  MDWF_TPU_DIR(4, 2, true)
+  MDWF_TPU_DIR(5, 2, false)
+  MDWF_TPU_DIR(6, 3, true)
+  MDWF_TPU_DIR(7, 3, false)
+#undef MDWF_TPU_DIR
+  // lane (g, c) writes colour c of units 8 t + g into the epilogue tile
+  if (c < 3) {
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      float* row = sA + (size_t)(warp * 32 + 8 * q + g) * kPadF + 2 * c;
+#pragma unroll
+      for (int sp = 0; sp < 4; sp++) {
+        row[6 * sp] = acc[8 * q + 2 * sp];
+        row[6 * sp + 1] = acc[8 * q + 2 * sp + 1];
+      }
+    }
+  }
+  epilogue<__half, float, EPI, true>(a, tl, t, nullptr, sA);
+}
+
+size_t tpu_smem_bytes(const Tiling& t) {
+  size_t base = (size_t)t.threads * kPadF * sizeof(float);
+  if (base < (size_t)t.threads * sizeof(double)) base = (size_t)t.threads * sizeof(double);
+  return base + (((size_t)t.nsb * 8 * sizeof(int) + 15) & ~(size_t)15) + (size_t)(t.threads / 32) * kTpuWords * 8;
+}
+
+bool tpu_usable(const Tiling& t, int L5) {
+  return t.threads % 32 == 0 && (L5 * t.rt) % 8 == 0 && tpu_smem_bytes(t) <= 200 * 1024;
+}
+
+template <int EPI>
+cudaError_t launch_tpu_one(const FastArgs<__half, float>& a, const Tiling& t, cudaStream_t st) {
+  const dim3 grid((unsigned)t.ntiles, (unsigned)t.ngroups);
+  const dim3 block((unsigned)t.rt, (unsigned)a.L5, (unsigned)t.nsb);
+  const size_t smem = tpu_smem_bytes(t);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(hop_tpu_kernel<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  hop_tpu_kernel<EPI><<<grid, block, smem, st>>>(a, t, a.F16);
+  return cudaGetLastError();
+}
+
 size_t mma_smem_bytes(const Tiling& t, int L5) {
   size_t base = (size_t)t.threads * kPadF * sizeof(float);
   if (base < (size_t)t.threads * sizeof(double)) base = (size_t)t.threads * sizeof(double);
@@ -1226,9 +1366,9 @@ int mma_max_threads() {
 }
 
 cudaError_t launch_fast_mma(const FastArgs<__half, float>& a, const Tiling& t, int epi, cudaStream_t st,
-                            const StageInfo* stage) {
+                            const StageInfo* stage, bool pipelined) {
   if (!mma_hop_usable(t, a.L5, a.N) || a.F16 == nullptr) return cudaErrorInvalidValue;
-  if (stage != nullptr && mma_bulk_usable(a, t)) {
+  if (pipelined && stage != nullptr && mma_bulk_usable(a, t)) {
     switch (epi) {
       case E_RAW: return launch_mma_bulk_one<E_RAW>(a, t, *stage, st);
       case E_BAINV: return launch_mma_bulk_one<E_BAINV>(a, t, *stage, st);
@@ -1236,6 +1376,17 @@ cudaError_t launch_fast_mma(const FastArgs<__half, float>& a, const Tiling& t, i
       case E_A_SAME: return launch_mma_bulk_one<E_A_SAME>(a, t, *stage, st);
       case E_AD_SAME_BD: return launch_mma_bulk_one<E_AD_SAME_BD>(a, t, *stage, st);
       case E_AINV_SAME: return launch_mma_bulk_one<E_AINV_SAME>(a, t, *stage, st);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  if (!pipelined && tpu_usable(t, a.L5)) {
+    switch (epi) {
+      case E_RAW: return launch_tpu_one<E_RAW>(a, t, st);
+      case E_BAINV: return launch_tpu_one<E_BAINV>(a, t, st);
+      case E_AINVD_BD: return launch_tpu_one<E_AINVD_BD>(a, t, st);
+      case E_A_SAME: return launch_tpu_one<E_A_SAME>(a, t, st);
+      case E_AD_SAME_BD: return launch_tpu_one<E_AD_SAME_BD>(a, t, st);
+      case E_AINV_SAME: return launch_tpu_one<E_AINV_SAME>(a, t, st);
       default: return cudaErrorInvalidValue;
     }
   }

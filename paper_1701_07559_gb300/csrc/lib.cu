@@ -427,10 +427,11 @@ struct FastOp {
   const StageInfo* stage = nullptr;   // neighbour staging through shared memory, when the tiling allows
   const uint32_t* F16 = nullptr;      // fp16 link fragments for the tensor-core hop
   bool mma = false;                   // use the tensor-core hop (fp16 storage only)
+  bool mma_pipelined = false;         // its bulk-copy pipelined form
 
   cudaError_t dispatch(const FastArgs<S, T>& a, int epi) const {
     if constexpr (std::is_same<S, __half>::value) {
-      if (mma) return launch_fast_mma(a, tl, epi, st, stage);
+      if (mma) return launch_fast_mma(a, tl, epi, st, stage, mma_pipelined);
     }
     return launch_fast<S, T>(a, tl, epi, st, stage);
   }
@@ -473,7 +474,7 @@ struct FastOp {
 // neighbour sites in shared memory when a block can hold whole sites (all N
 // slots of nsb sites, at most ~200 KB of staging); FP64 runs unstaged.
 // Hop kernel variants: 0 automatic, 1 CUDA-core direct loads, 2 CUDA-core staged, 3 tensor-core (fp16).
-enum { HOP_AUTO = 0, HOP_DIRECT = 1, HOP_STAGED = 2, HOP_MMA = 3, HOP_TUNE_ALL = 4 };
+enum { HOP_AUTO = 0, HOP_DIRECT = 1, HOP_STAGED = 2, HOP_MMA = 3, HOP_TUNE_ALL = 4, HOP_MMA_PIPE = 5 };
 
 template <typename S>
 Tiling fast_tiling(const Geom& g, int L5, int N, int nsb_req, bool* staged, bool allow_staging);
@@ -485,6 +486,8 @@ void choose_hop(FastOp<S, T>& op, const Cfg* cfg, int nsb_req, int variant, cons
   const int L5 = op.L5, N = op.N, upb = L5 * N;
   bool staged = false;
   op.mma = false;
+  op.mma_pipelined = variant == HOP_MMA_PIPE;
+  if (variant == HOP_MMA_PIPE) variant = HOP_MMA;
   op.stage = nullptr;
   op.F16 = cfg->F16;
   if (variant == HOP_MMA && std::is_same<S, __half>::value && cfg->F16) {
@@ -655,7 +658,7 @@ struct BatchSolver {
     stage.err = errw;
     // the wait-timeout test needs a kernel with waits: the staged one, or the
     // pipelined tensor-core one when that variant is asked for
-    const int variant = o.timeout_test ? (o.hop_variant == HOP_MMA ? HOP_MMA : HOP_STAGED) : o.hop_variant;
+    const int variant = o.timeout_test ? (o.hop_variant == HOP_MMA_PIPE ? HOP_MMA_PIPE : HOP_STAGED) : o.hop_variant;
     choose_hop(op64, cf, 0, HOP_DIRECT, &stage);
     choose_hop(op32, cf, nsb, (variant == HOP_AUTO || variant == HOP_TUNE_ALL) ? HOP_DIRECT : variant, &stage);
     choose_hop(opS, cf, nsb, (variant == HOP_AUTO || variant == HOP_TUNE_ALL) ? HOP_DIRECT : variant, &stage);

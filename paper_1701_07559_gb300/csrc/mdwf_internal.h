@@ -354,8 +354,10 @@ cudaError_t launch_fast(const FastArgs<S, T>& a, const Tiling& t, int epi, cudaS
 bool mma_hop_usable(const Tiling& t, int L5, int N);
 int mma_max_threads();
 // stage: bound and status word of the waits of the pipelined form (null: unpipelined form)
+// pipelined: the bulk-copy double-buffered form (needs stage), else the thread-per-unit
+// form when the tiling allows it (whole warps, L5 rt a multiple of 8), else the tile form
 cudaError_t launch_fast_mma(const FastArgs<__half, float>& a, const Tiling& t, int epi, cudaStream_t st,
-                            const StageInfo* stage);
+                            const StageInfo* stage, bool pipelined);
 cudaError_t build_link_frags(const double* U64, uint32_t* frag, long nlinks, cudaStream_t st);
 // Wilson flow (flow.cu): U in the C ABI gauge layout, Z: workspace of 3 * 4V * 18 doubles.
 cudaError_t wilson_flow(double* U, const int L[4], double eps, int nsteps, double* Z, cudaStream_t st);
