@@ -263,6 +263,18 @@ int mdwf_session_occupied(const mdwf_session* s);
 /* mdwf_make_source on device fields (eta4d: V * 24 doubles; src5d: L5 * V * 24), on `stream`. */
 int mdwf_make_source_dev(mdwf_ctx* ctx, int cfg_id, const double* eta4d, double* src5d, void* stream);
 
+/* Residual-mass correlators (Eq. mres, Sec. III): for the n 5D solutions xs
+ * (device, API layout; the solves of point sources, one per source spin and
+ * colour), per time slice t (host arrays of Lt doubles)
+ *   c_pp[t]  = sum_{x in t, sources, spin, colour} |q(x)|^2,  q = P_- x_0 + P_+ x_{L5-1}
+ *   c_j5q[t] = the same for Q = P_+ x_{L5/2-1} + P_- x_{L5/2} (the midpoint field),
+ * P_+- = (1 +- gamma_5) / 2.  With the sources of mdwf_make_source these are the
+ * pseudoscalar and midpoint-pseudoscalar correlators of the paper's ratio, and
+ * m_res(t) = c_j5q[t] / c_pp[t].  FP64, fixed summation order.  Errors: ARG,
+ * STATE, NOMEM, CUDA. */
+int mdwf_mres_correlators_dev(mdwf_ctx* ctx, int cfg_id, int n, double* const* xs, double* c_pp, double* c_j5q,
+                              void* stream);
+
 /* The autotuner on its own: the inner hop form and sites per block that the
  * solver uses for n right-hand sides of this configuration at `precision`
  * (include_tensor_core: also try the tensor-core hop), with its time for one

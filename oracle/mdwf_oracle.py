@@ -27,6 +27,8 @@ What is computed, and where it comes from (arXiv:1701.07559):
   form, the one Chroma used):  Mhat = A_ee - D_eo A_oo^-1 D_oe  with
   A = (b5 d + 1) + (c5 d - 1) P, B = b5 + c5 P, d = 4 - M5, D_eo = -1/2 H_eo B.
 * Conjugate gradient on the normal equations (Sec. VII: the solver QUDA runs).
+* The residual-mass correlators of Sec. III (midpoint and wall pseudoscalar
+  densities, equation eq:mres).
 
 Gamma matrices: DeGrand-Rossi chiral basis (gamma_5 = diag(1,1,-1,-1)).
 Boundary conditions: periodic in x, y, z; antiperiodic in t.
@@ -396,6 +398,32 @@ def hopping_at_site(U, psi, site, antiperiodic_t=True, dagger=False):
         out += phase_f * np.einsum('st,ab,ntb->nsa', ID4 + sgn * GAMMA[mu], Uf, pf)
         out += phase_b * np.einsum('st,ab,ntb->nsa', ID4 - sgn * GAMMA[mu], Ub, pb)
     return out
+
+
+# ---------------------------------------------------------------------------
+# Residual mass
+# ---------------------------------------------------------------------------
+def mres_correlators(xs):
+    """Correlators of the residual-mass ratio (Sec. III, equation eq:mres).
+
+    xs: the 5D solutions of the point-source solves (one per source spin and
+    colour), each [s, t, z, y, x, spin, colour].  The wall quark field is
+    q = P_- x_0 + P_+ x_{L5-1} and the midpoint field Q = P_+ x_{L5/2-1} +
+    P_- x_{L5/2}; summed over the spatial sites of each time slice and over
+    the sources, the pseudoscalar correlators are the squared norms of q and
+    of Q (gamma_5-hermiticity of the sources' propagator).  Returns
+    (c_pp[t], c_j5q[t]); m_res(t) = c_j5q / c_pp.
+    """
+    L5 = xs[0].shape[0]
+    Lt = xs[0].shape[1]
+    c_pp = np.zeros(Lt)
+    c_j5q = np.zeros(Lt)
+    for x in xs:
+        q = spin_mul(P_MINUS, x[0]) + spin_mul(P_PLUS, x[L5 - 1])
+        Q = spin_mul(P_PLUS, x[L5 // 2 - 1]) + spin_mul(P_MINUS, x[L5 // 2])
+        c_pp += np.sum(np.abs(q) ** 2, axis=(1, 2, 3, 4, 5))
+        c_j5q += np.sum(np.abs(Q) ** 2, axis=(1, 2, 3, 4, 5))
+    return c_pp, c_j5q
 
 
 # ---------------------------------------------------------------------------

@@ -297,6 +297,50 @@ __global__ void k_z2(unsigned long long seed, double* __restrict__ eta, long n) 
   eta[2 * k + 1] = 0.0;
 }
 
+// Residual-mass correlators (Eq. mres of arXiv:1701.07559): per 4D site, summed
+// over the n solutions (spin-colour sources), the squared norms of the wall field
+// q = P_- x_0 + P_+ x_{L5-1} and of the midpoint field Q = P_+ x_{L5/2-1} + P_- x_{L5/2};
+// P_+ keeps spins 0, 1 and P_- spins 2, 3 (gamma_5 = diag(1, 1, -1, -1)).  FP64,
+// solutions in the C ABI 5D layout.
+__global__ void k_mres_sites(const double* const* __restrict__ xs, int n, long V, int L5, double* pp, double* j5) {
+  const long x = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= V) return;
+  const int sm = L5 / 2;
+  double a = 0.0, b = 0.0;
+  for (int k = 0; k < n; k++) {
+    const double* f = xs[k];
+    const double* w0 = f + (x) * 24;                          // s = 0
+    const double* wl = f + ((long)(L5 - 1) * V + x) * 24;     // s = L5 - 1
+    const double* m0 = f + ((long)(sm - 1) * V + x) * 24;     // s = L5/2 - 1
+    const double* m1 = f + ((long)sm * V + x) * 24;           // s = L5/2
+    for (int i = 0; i < 12; i++) {                            // spins 0, 1: (re, im) x 3 colours x 2
+      a += wl[i] * wl[i];
+      b += m0[i] * m0[i];
+    }
+    for (int i = 12; i < 24; i++) {                           // spins 2, 3
+      a += w0[i] * w0[i];
+      b += m1[i] * m1[i];
+    }
+  }
+  pp[x] = a;
+  j5[x] = b;
+}
+
+// Per time slice, fixed-order sums of the site values (one block per slice).
+__global__ void k_slice_sum(const double* __restrict__ v, long slice, double* out) {
+  __shared__ double sh[256];
+  const double* p = v + (long)blockIdx.x * slice;
+  double s = 0.0;
+  for (long i = threadIdx.x; i < slice; i += 256) s += p[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = sh[0];
+}
+
 // rho = S(bhat - q) with bhat in FP64 and q in FP32 (the residual of a reliable
 // update computed with FP32 arithmetic); partial |bhat - q|^2 in FP64.
 template <typename S>
@@ -424,6 +468,14 @@ cudaError_t walls(const double* eta, double* w, long V, int L5, cudaStream_t st)
 cudaError_t z2_source(unsigned long long seed, double* eta, long V, cudaStream_t st) {
   const long n = V * 12;
   k_z2<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(seed, eta, n);
+  return cudaGetLastError();
+}
+
+cudaError_t mres_correlators(const double* const* xs, int n, long V, int Lt, int L5, double* pp, double* j5,
+                             double* c_pp, double* c_j5, cudaStream_t st) {
+  k_mres_sites<<<(unsigned)((V + 255) / 256), 256, 0, st>>>(xs, n, V, L5, pp, j5);
+  k_slice_sum<<<Lt, 256, 0, st>>>(pp, V / Lt, c_pp);
+  k_slice_sum<<<Lt, 256, 0, st>>>(j5, V / Lt, c_j5);
   return cudaGetLastError();
 }
 

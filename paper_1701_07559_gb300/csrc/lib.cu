@@ -2004,6 +2004,32 @@ int mdwf_plaquette_dev(mdwf_ctx* ctx, const double* U, double* plaq) {
   return MDWF_OK;
 }
 
+int mdwf_mres_correlators_dev(mdwf_ctx* ctx, int cfg_id, int n, double* const* xs, double* c_pp, double* c_j5q,
+                              void* stream) {
+  if (!ctx) return MDWF_ERR_ARG;
+  Cfg* cfg;
+  int rc = check_cfg(ctx, cfg_id, &cfg);
+  if (rc) return rc;
+  if (n < 1 || !xs || !c_pp || !c_j5q) return fail(ctx, MDWF_ERR_ARG, "mres_correlators: bad arguments");
+  for (int i = 0; i < n; i++)
+    if (!xs[i]) return fail(ctx, MDWF_ERR_ARG, "mres_correlators: null solution");
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = pick_stream(ctx, stream);
+  const long V = ctx->g.V;
+  const int Lt = ctx->g.L[3];
+  cudaError_t e = cudaSuccess;
+  double** dptr = (double**)ws_get(ctx, "mres.ptrs", sizeof(double*) * n, &e);
+  CK(e);
+  double* site = (double*)ws_get(ctx, "mres.site", sizeof(double) * (2 * V + 2 * Lt), &e);
+  CK(e);
+  CK(cudaMemcpyAsync(dptr, xs, sizeof(double*) * n, cudaMemcpyHostToDevice, st));
+  CK(mres_correlators(dptr, n, V, Lt, cfg->act.L5, site, site + V, site + 2 * V, site + 2 * V + Lt, st));
+  CK(cudaMemcpyAsync(c_pp, site + 2 * V, sizeof(double) * Lt, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(c_j5q, site + 2 * V + Lt, sizeof(double) * Lt, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return MDWF_OK;
+}
+
 int mdwf_extract_prop4d(const double* x5d, const int dims[4], int L5, double* q4d) {
   if (!x5d || !dims || !q4d || L5 < 1) return MDWF_ERR_ARG;
   long V = 1;

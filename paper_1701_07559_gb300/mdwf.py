@@ -103,6 +103,7 @@ _sig = {
     'mdwf_z2_source_dev': (_I, [_P, ctypes.c_ulonglong, _P, _P]),
     'mdwf_wilson_flow_dev': (_I, [_P, _P, _D, _I, _P]),
     'mdwf_plaquette_dev': (_I, [_P, _P, ctypes.POINTER(_D)]),
+    'mdwf_mres_correlators_dev': (_I, [_P, _I, _I, ctypes.POINTER(_P), _P, _P, _P]),
     'mdwf_autotune': (_I, [_P, _I, _I, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_D)]),
 }
 for _name, (_res, _args) in _sig.items():
@@ -416,6 +417,20 @@ def flowed_gauge_dev(ctx, U_host, flow_t=1.0, flow_eps=0.01):
     U = torch.from_numpy(np.ascontiguousarray(U_host, dtype=np.complex128)).to('cuda')
     mdwf_wilson_flow_dev(ctx, U, flow_eps, int(round(flow_t / flow_eps)))
     return U.cpu().numpy()
+
+
+def mdwf_mres_correlators_dev(ctx, cfg_id, xs, stream=None):
+    """Residual-mass correlators of the solutions xs (torch CUDA 5D fields):
+    returns (c_pp, c_j5q) as numpy arrays over the time slices."""
+    shape = _shape5(ctx, cfg_id)
+    n = len(xs)
+    xp = (_P * n)(*[_dev_ptr(x, shape) for x in xs])
+    Lt = ctx.dims[3]
+    pp = np.empty(Lt)
+    j5 = np.empty(Lt)
+    sh = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+    _check(ctx, _lib.mdwf_mres_correlators_dev(ctx.handle, int(cfg_id), n, xp, _ptr(pp), _ptr(j5), sh))
+    return pp, j5
 
 
 def mdwf_autotune(ctx, cfg_id, n, precision=MDWF_PREC_HALF, include_tensor_core=False):

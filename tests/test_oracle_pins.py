@@ -429,3 +429,39 @@ def test_sampled_site_operator_equals_full_operator():
         got = sampled.dx_at_site(U, x, site, *act)
         xs, ys, zs, ts = site
         assert np.abs(got - full[:, ts, zs, ys, xs]).max() < 1e-13
+
+
+def test_mres_correlators_l5_two_identity_and_hand_example():
+    """L5 = 2: the wall field q and the midpoint field Q take complementary
+    chiral halves of the same two slices, so c_pp + c_j5q is the full norm of
+    the solution per time slice; a single component lands in exactly one."""
+    dims, L5 = (2, 2, 2, 4), 2
+    xs = [synth.gaussian_spinor((L5, 4, 2, 2, 2, 4, 3), 60 + k) for k in range(3)]
+    pp, j5 = O.mres_correlators(xs)
+    full = sum(np.sum(np.abs(x) ** 2, axis=(0, 2, 3, 4, 5, 6)) for x in xs)
+    assert np.allclose(pp + j5, full, rtol=1e-14)
+    L5 = 6
+    x = np.zeros((L5, 3, 2, 2, 2, 4, 3), dtype=np.complex128)
+    x[0, 1, 0, 0, 0, 2, 1] = 2.0            # s = 0, spin 2: P_- keeps it -> q
+    x[2, 2, 0, 1, 0, 0, 0] = 3.0            # s = L5/2 - 1, spin 0: P_+ keeps it -> Q
+    x[3, 2, 0, 1, 0, 1, 0] = 5.0            # s = L5/2, spin 1: P_- drops it
+    pp, j5 = O.mres_correlators([x])
+    assert np.array_equal(pp, [0.0, 4.0, 0.0]) and np.array_equal(j5, [0.0, 0.0, 9.0])
+
+
+def test_mres_falls_with_l5_free_shamir():
+    """Free field, Shamir (b5 = 1, c5 = 0): the midpoint correlator, relative to
+    the pseudoscalar one, falls geometrically with L5 (the leakage of the wall
+    modes through the bulk), from the momentum-space solutions."""
+    dims, M5, mf = (2, 2, 2, 6), 1.3, 0.05
+    ratios = []
+    for L5 in (4, 6, 8):
+        xs = []
+        for spin in range(4):
+            for colour in range(3):
+                s0 = 0 if spin < 2 else L5 - 1      # the wall-injected source (c5 = 0): P_+ at s=0, P_- at L5-1
+                xs.append(O.free_propagator_point(dims, L5, M5, 1.0, 0.0, mf, spin, colour, s0))
+        pp, j5 = O.mres_correlators(xs)
+        assert np.all(pp > 0) and np.all(j5 > 0)
+        ratios.append(np.sum(j5) / np.sum(pp))
+    assert ratios[1] < 0.5 * ratios[0] and ratios[2] < 0.5 * ratios[1]
