@@ -377,7 +377,7 @@ __global__ void k_beta(Scal c, int N) {
 // reached tau |bhat|, when it fell below the stopping norm (the FP64 residual
 // decides), or when it did not halve since the previous FP32 update (its
 // accuracy floor).  Convergence is accepted on the FP32 residual alone only
-// when bhat itself is within 10^3 of the stopping norm.
+// when bhat itself is within 10^3 of the stopping norm.  (tau = 1e-5.)
 __global__ void k_after_update(Scal c, int N, const int* um) {
   int r = threadIdx.x;
   if (r < N && um[r]) {
@@ -967,7 +967,7 @@ int solve_batch_impl(mdwf_ctx* ctx, Cfg* cfg, int n, const double* const* srcs, 
   }
   CK(cudaMemcpyAsync(sv.sc.stop2, stop2.data(), sizeof(double) * N, cudaMemcpyHostToDevice, st));
   sv.sc.delta2 = BatchSolver<S>::kFP64 ? 0.0 : o.delta * o.delta;
-  sv.sc.tau2 = BatchSolver<S>::kFP64 ? 0.0 : 1e-6;
+  sv.sc.tau2 = BatchSolver<S>::kFP64 ? 0.0 : 1e-10;
   // bhat_e = b_e + 1/2 H_eo B A^-1 b_o   (B A^-1 on the odd sites with the dense table kernel)
   {
     Op<double, double> loc;
@@ -1179,7 +1179,7 @@ struct SessionImpl : SessionBase {
     int rc = sv.init(c, cf, masses, o.nsb, o.profile != 0, o, s);
     if (rc) return rc;
     sv.sc.delta2 = BatchSolver<S>::kFP64 ? 0.0 : o.delta * o.delta;
-    sv.sc.tau2 = BatchSolver<S>::kFP64 ? 0.0 : 1e-6;
+    sv.sc.tau2 = BatchSolver<S>::kFP64 ? 0.0 : 1e-10;
     cudaError_t e = cudaSuccess;
     fmask = (int*)ws_get(c, prefix + "fmask", sizeof(int) * N, &e);
     CK(e);
