@@ -99,9 +99,10 @@ class Server:
     """Continuous-batching server over resident gauge configurations (one device)."""
 
     def __init__(self, device=0, hbm_budget=None, tol=1e-10, precision='half', chunk=16, max_slots=12,
-                 keep_solutions=False, opts=None, clock=time.perf_counter, lib=None):
+                 keep_solutions=False, opts=None, clock=time.perf_counter, lib=None, priorities=False):
         """lib: the binding module (default: the libmdwf binding); a stand-in with the
-        same session functions drives the host logic without a device (tests)."""
+        same session functions drives the host logic without a device (tests).
+        priorities: rank the configurations' streams by request cost (see _prioritise)."""
         import torch
         self.torch = torch
         self.lib = lib if lib is not None else M
@@ -125,6 +126,7 @@ class Server:
         self.samples = []            # (time, queued, running, bytes in use)
         self.done = []
         self.cv = threading.Condition(threading.RLock())
+        self.priorities = bool(priorities)
 
     # --- configurations -------------------------------------------------------
     def add_config(self, name, dims, U, M5, b5, c5, mf, L5, t_antiperiodic=1):
@@ -141,16 +143,17 @@ class Server:
         self._prioritise()
 
     def _prioritise(self):
-        """Give every configuration a stream whose priority ranks it by the cost of
-        one request (smallest lattice first): the device then schedules the
-        blocks of cheap requests ahead of queued blocks of expensive ones
-        (shortest job first), which bounds their latency under a mixed load."""
+        """Give every configuration its own stream.  With priorities, the stream
+        priority ranks the configuration by the cost of one request (smallest
+        lattice first): the device then schedules the blocks of cheap requests
+        ahead of queued blocks of expensive ones (shortest job first)."""
         if not self.on_gpu:
             return
         order = sorted(self.configs.values(), key=lambda c: c.field_bytes)
         for rank, c in enumerate(order):
             if c.session is None:
-                c.stream = self.torch.cuda.Stream(self.dev, priority=-(len(order) - 1 - rank))
+                prio = -(len(order) - 1 - rank) if self.priorities else 0
+                c.stream = self.torch.cuda.Stream(self.dev, priority=prio)
 
     def close(self):
         for c in self.configs.values():
