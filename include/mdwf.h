@@ -297,6 +297,15 @@ int mdwf_wilson_flow_dev(mdwf_ctx* ctx, double* U, double eps, int nsteps, void*
  * field U (layout as above); synchronous, result in *plaq (host). */
 int mdwf_plaquette_dev(mdwf_ctx* ctx, const double* U, double* plaq);
 
+/* Gauge-covariant Gaussian smearing of a 4D source in place (device field eta4d,
+ * V * 24 doubles, the mdwf_make_source layout): n_iter steps of
+ *   eta <- eta + k sum_{i=x,y,z} [U_i(x) eta(x+i) + U_i(x-i)^+ eta(x-i) - 2 eta(x)],
+ * k = sigma^2 / (4 n_iter), on the links of cfg_id (which tends to
+ * exp(sigma^2 Delta / 4) eta; a point source spreads to variance sigma^2 / 2 per
+ * direction).  The paper's propagators use gauge-covariant Gaussian-smeared
+ * sources (Sec. VII); it does not give the width.  FP64.  Errors: ARG, STATE, NOMEM, CUDA. */
+int mdwf_smear_source_dev(mdwf_ctx* ctx, int cfg_id, double* eta4d, double sigma, int n_iter, void* stream);
+
 /* Z2 noise 4D source on a device field eta4d (V * 24 doubles), on `stream`:
  * complex element k ([t][z][y][x][spin][colour] order) is +1 or -1 (imaginary
  * part 0) by the top bit of the k-th output of SplitMix64 started from `seed`

@@ -29,6 +29,7 @@ What is computed, and where it comes from (arXiv:1701.07559):
 * Conjugate gradient on the normal equations (Sec. VII: the solver QUDA runs).
 * The residual-mass correlators of Sec. III (midpoint and wall pseudoscalar
   densities, equation eq:mres).
+* Gauge-covariant Gaussian smearing of 4D sources (Sec. VII's propagators).
 
 Gamma matrices: DeGrand-Rossi chiral basis (gamma_5 = diag(1,1,-1,-1)).
 Boundary conditions: periodic in x, y, z; antiperiodic in t.
@@ -398,6 +399,29 @@ def hopping_at_site(U, psi, site, antiperiodic_t=True, dagger=False):
         out += phase_f * np.einsum('st,ab,ntb->nsa', ID4 + sgn * GAMMA[mu], Uf, pf)
         out += phase_b * np.einsum('st,ab,ntb->nsa', ID4 - sgn * GAMMA[mu], Ub, pb)
     return out
+
+
+# ---------------------------------------------------------------------------
+# Gauge-covariant Gaussian source smearing
+# ---------------------------------------------------------------------------
+def covariant_laplacian_3d(U, eta):
+    """(Delta eta)(x) = sum_{i=x,y,z} [U_i(x) eta(x+i) + U_i(x-i)^+ eta(x-i) - 2 eta(x)], on a 4D
+    field [t, z, y, x, spin, colour] (spin-diagonal; no hop in time)."""
+    out = -6.0 * eta
+    for mu in range(3):
+        out = out + colour_mul(U[..., mu, :, :], _shift(eta, mu, +1, False, 0))
+        Ub = np.conj(np.swapaxes(U[..., mu, :, :], -1, -2))
+        out = out + _shift(colour_mul(Ub, eta), mu, -1, False, 0)
+    return out
+
+
+def gaussian_smear(U, eta, sigma, n_iter):
+    """Gauge-covariant Gaussian smearing of a 4D source (the sources of Sec. VII's propagators):
+    eta <- (1 + sigma^2 / (4 n) Delta)^n eta, which tends to exp(sigma^2 Delta / 4) eta."""
+    k = sigma * sigma / (4.0 * n_iter)
+    for _ in range(n_iter):
+        eta = eta + k * covariant_laplacian_3d(U, eta)
+    return eta
 
 
 # ---------------------------------------------------------------------------

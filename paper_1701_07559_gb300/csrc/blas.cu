@@ -297,6 +297,52 @@ __global__ void k_z2(unsigned long long seed, double* __restrict__ eta, long n) 
   eta[2 * k + 1] = 0.0;
 }
 
+// One step of gauge-covariant Gaussian source smearing on a 4D field (the sources
+// of the paper's propagators, Sec. VII):
+//   out(x) = in(x) + k sum_{i = x,y,z} [U_i(x) in(x+i) + U_i(x-i)^+ in(x-i) - 2 in(x)],
+// spin-diagonal, no hop in time.  in / out: C ABI layout [t][z][y][x][spin][colour];
+// U: the context's FP64 links [parity][h][mu][18], h = lex / 2.
+__global__ void k_smear_step(const double* __restrict__ U, const double* __restrict__ in, double* __restrict__ out,
+                             Geom g, double k) {
+  const long lex = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (lex >= g.V) return;
+  int c[4];
+  long r = lex;
+  for (int i = 0; i < 4; i++) { c[i] = (int)(r % g.L[i]); r /= g.L[i]; }
+  const double* me = in + lex * 24;
+  double acc[24];
+  for (int i = 0; i < 24; i++) acc[i] = (1.0 - 6.0 * k) * me[i];
+  long stride = 1;
+  for (int mu = 0; mu < 3; mu++) {
+    const int Lm = g.L[mu];
+    const long fw = c[mu] == Lm - 1 ? lex - (long)(Lm - 1) * stride : lex + stride;
+    const long bw = c[mu] == 0 ? lex + (long)(Lm - 1) * stride : lex - stride;
+    const int pf = (c[0] + c[1] + c[2] + c[3]) & 1;
+    const double* uf = U + (((long)pf * g.Vh + (lex >> 1)) * 4 + mu) * 18;            // U_mu(x)
+    const double* ub = U + (((long)(1 - pf) * g.Vh + (bw >> 1)) * 4 + mu) * 18;       // U_mu(x - mu)
+    const double* pf_in = in + fw * 24;
+    const double* pb_in = in + bw * 24;
+    for (int sp = 0; sp < 4; sp++)
+      for (int a = 0; a < 3; a++) {
+        double re = 0.0, im = 0.0;
+        for (int b = 0; b < 3; b++) {
+          const double fr = uf[2 * (3 * a + b)], fi = uf[2 * (3 * a + b) + 1];      // U_ab
+          const double vr = pf_in[6 * sp + 2 * b], vi = pf_in[6 * sp + 2 * b + 1];
+          re += fr * vr - fi * vi;
+          im += fr * vi + fi * vr;
+          const double br = ub[2 * (3 * b + a)], bi = -ub[2 * (3 * b + a) + 1];     // (U^+)_ab = conj(U_ba)
+          const double wr = pb_in[6 * sp + 2 * b], wi = pb_in[6 * sp + 2 * b + 1];
+          re += br * wr - bi * wi;
+          im += br * wi + bi * wr;
+        }
+        acc[6 * sp + 2 * a] += k * re;
+        acc[6 * sp + 2 * a + 1] += k * im;
+      }
+    stride *= Lm;
+  }
+  for (int i = 0; i < 24; i++) out[lex * 24 + i] = acc[i];
+}
+
 // Residual-mass correlators (Eq. mres of arXiv:1701.07559): per 4D site, summed
 // over the n solutions (spin-colour sources), the squared norms of the wall field
 // q = P_- x_0 + P_+ x_{L5-1} and of the midpoint field Q = P_+ x_{L5/2-1} + P_- x_{L5/2};
@@ -468,6 +514,11 @@ cudaError_t walls(const double* eta, double* w, long V, int L5, cudaStream_t st)
 cudaError_t z2_source(unsigned long long seed, double* eta, long V, cudaStream_t st) {
   const long n = V * 12;
   k_z2<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(seed, eta, n);
+  return cudaGetLastError();
+}
+
+cudaError_t smear_step(const double* U, const double* in, double* out, const Geom& g, double k, cudaStream_t st) {
+  k_smear_step<<<(unsigned)((g.V + 127) / 128), 128, 0, st>>>(U, in, out, g, k);
   return cudaGetLastError();
 }
 

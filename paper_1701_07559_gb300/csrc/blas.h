@@ -51,6 +51,7 @@ cudaError_t zero_masked(S* v, float* nrm, const Tiling& t, long Vh, int L5, int 
 
 cudaError_t walls(const double* eta, double* w, long V, int L5, cudaStream_t st);
 cudaError_t z2_source(unsigned long long seed, double* eta, long V, cudaStream_t st);
+cudaError_t smear_step(const double* U, const double* in, double* out, const Geom& g, double k, cudaStream_t st);
 cudaError_t mres_correlators(const double* const* xs, int n, long V, int Lt, int L5, double* pp, double* j5,
                              double* c_pp, double* c_j5, cudaStream_t st);
 

@@ -2030,6 +2030,30 @@ int mdwf_mres_correlators_dev(mdwf_ctx* ctx, int cfg_id, int n, double* const* x
   return MDWF_OK;
 }
 
+int mdwf_smear_source_dev(mdwf_ctx* ctx, int cfg_id, double* eta4d, double sigma, int n_iter, void* stream) {
+  if (!ctx) return MDWF_ERR_ARG;
+  auto it = ctx->cfgs.find(cfg_id);
+  if (it == ctx->cfgs.end() || !it->second.has_gauge) return fail(ctx, MDWF_ERR_STATE, "no gauge field for cfg_id");
+  if (!eta4d || n_iter < 0 || !(sigma >= 0) || !std::isfinite(sigma))
+    return fail(ctx, MDWF_ERR_ARG, "smear_source_dev: bad arguments");
+  if (n_iter == 0 || sigma == 0.0) return MDWF_OK;
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = pick_stream(ctx, stream);
+  cudaError_t e = cudaSuccess;
+  double* tmp = (double*)ws_get(ctx, "smear.tmp", sizeof(double) * 24 * (size_t)ctx->g.V, &e);
+  CK(e);
+  const double k = sigma * sigma / (4.0 * n_iter);
+  double* a = eta4d;
+  double* b = tmp;
+  for (int i = 0; i < n_iter; i++) {
+    CK(smear_step(it->second.U64, a, b, ctx->g, k, st));
+    std::swap(a, b);
+  }
+  if (a != eta4d) CK(cudaMemcpyAsync(eta4d, a, sizeof(double) * 24 * (size_t)ctx->g.V, cudaMemcpyDeviceToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  return MDWF_OK;
+}
+
 int mdwf_extract_prop4d(const double* x5d, const int dims[4], int L5, double* q4d) {
   if (!x5d || !dims || !q4d || L5 < 1) return MDWF_ERR_ARG;
   long V = 1;

@@ -103,6 +103,7 @@ _sig = {
     'mdwf_z2_source_dev': (_I, [_P, ctypes.c_ulonglong, _P, _P]),
     'mdwf_wilson_flow_dev': (_I, [_P, _P, _D, _I, _P]),
     'mdwf_plaquette_dev': (_I, [_P, _P, ctypes.POINTER(_D)]),
+    'mdwf_smear_source_dev': (_I, [_P, _I, _P, _D, _I, _P]),
     'mdwf_mres_correlators_dev': (_I, [_P, _I, _I, ctypes.POINTER(_P), _P, _P, _P]),
     'mdwf_autotune': (_I, [_P, _I, _I, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_D)]),
 }
@@ -417,6 +418,14 @@ def flowed_gauge_dev(ctx, U_host, flow_t=1.0, flow_eps=0.01):
     U = torch.from_numpy(np.ascontiguousarray(U_host, dtype=np.complex128)).to('cuda')
     mdwf_wilson_flow_dev(ctx, U, flow_eps, int(round(flow_t / flow_eps)))
     return U.cpu().numpy()
+
+
+def mdwf_smear_source_dev(ctx, cfg_id, eta, sigma, n_iter, stream=None):
+    """Gauge-covariant Gaussian smearing of a 4D source (torch CUDA tensor) in place."""
+    d = ctx.dims
+    sh = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+    _check(ctx, _lib.mdwf_smear_source_dev(ctx.handle, int(cfg_id), _dev_ptr(eta, (d[3], d[2], d[1], d[0], 4, 3)),
+                                           float(sigma), int(n_iter), sh))
 
 
 def mdwf_mres_correlators_dev(ctx, cfg_id, xs, stream=None):

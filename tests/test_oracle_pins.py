@@ -465,3 +465,45 @@ def test_mres_falls_with_l5_free_shamir():
         assert np.all(pp > 0) and np.all(j5 > 0)
         ratios.append(np.sum(j5) / np.sum(pp))
     assert ratios[1] < 0.5 * ratios[0] and ratios[2] < 0.5 * ratios[1]
+
+
+def test_gaussian_smearing_free_field_plane_wave():
+    """Free field: a plane wave is an eigenvector of the smearing with eigenvalue
+    (1 + k sum_i (2 cos p_i - 2))^n, k = sigma^2 / (4 n); time is not smeared."""
+    dims = (4, 6, 2, 5)
+    Lx, Ly, Lz, Lt = dims
+    U = synth.unit_gauge(dims)
+    p = (2 * np.pi * 1 / Lx, 2 * np.pi * 2 / Ly, 2 * np.pi * 1 / Lz, 2 * np.pi * 3 / Lt)
+    t, z, y, x = np.meshgrid(range(Lt), range(Lz), range(Ly), range(Lx), indexing='ij')
+    phase = np.exp(1j * (p[0] * x + p[1] * y + p[2] * z + p[3] * t))
+    chi = synth.gaussian_spinor((4, 3), 5)
+    eta = phase[..., None, None] * chi
+    sigma, n = 2.0, 7
+    k = sigma ** 2 / (4 * n)
+    lam = (1 + k * sum(2 * np.cos(p[i]) - 2 for i in range(3))) ** n
+    assert np.abs(O.gaussian_smear(U, eta, sigma, n) - lam * eta).max() < 1e-13
+
+
+def test_gaussian_smearing_covariance_and_width():
+    dims = (4, 4, 2, 3)
+    U = synth.random_gauge(dims, 31, 0.7)
+    eta = synth.gaussian_spinor((3, 2, 4, 4, 4, 3), 32)
+    W = synth.gauge_rotation(dims, 33)
+    UW = np.empty_like(U)
+    for mu, ax in enumerate((3, 2, 1, 0)):
+        UW[..., mu, :, :] = W @ U[..., mu, :, :] @ np.conj(np.swapaxes(np.roll(W, -1, axis=ax), -1, -2))
+    a = O.gaussian_smear(UW, np.einsum('tzyxab,tzyxsb->tzyxsa', W, eta), 1.5, 4)
+    b = np.einsum('tzyxab,tzyxsb->tzyxsa', W, O.gaussian_smear(U, eta, 1.5, 4))
+    assert np.abs(a - b).max() < 1e-13
+    # free field: each step spreads a point by variance 2k per direction, so n steps give 2 k n = sigma^2 / 2
+    # (24 sites per direction: the support of 10 steps stays clear of the wrap-around)
+    big = (24, 24, 24, 1)
+    eta = np.zeros((1, 24, 24, 24, 4, 3), dtype=np.complex128)
+    eta[0, 12, 12, 12, 0, 0] = 1.0
+    sigma, n = 2.0, 10
+    sm = O.gaussian_smear(synth.unit_gauge(big), eta, sigma, n)[0, ..., 0, 0].real
+    c = np.arange(24) - 12
+    for axis in range(3):
+        w = sm.sum(axis=tuple(a for a in range(3) if a != axis))
+        assert abs(w.sum() - 1.0) < 1e-13
+        assert abs((w * c ** 2).sum() - sigma ** 2 / 2) < 1e-12
