@@ -48,6 +48,8 @@ def parse():
                     help='0 autotuned (CUDA-core forms), 1 CUDA-core direct loads, 2 CUDA-core staged, '
                          '3 tensor-core (fp16), 4 autotuned including the tensor-core form')
     ap.add_argument('--nsb', type=int, default=0, help='sites per thread block (0: chosen by the library)')
+    ap.add_argument('--schur', default='asym', choices=['asym', 'sym'],
+                    help='Schur form of the solve: asymmetric (default) or symmetric')
     ap.add_argument('--requests', type=int, default=300, help='serve mode: requests per arrival rate')
     ap.add_argument('--rates', default='0.5,0.9,1.2', help='serve mode: arrival rates as fractions of capacity')
     ap.add_argument('--serve-lattices', default='16,16,16,48:12;24,24,24,64:8;32,32,32,96:6',
@@ -251,7 +253,8 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     dsrc = [torch.from_numpy(s).to('cuda') for s in srcs]
     dx = [torch.empty_like(s) for s in dsrc]
-    opts = M.mdwf_default_opts(precision=prec, profile=1, hop_variant=args.hop_variant, nsb=args.nsb)
+    schur = 1 if args.schur == 'sym' else 0
+    opts = M.mdwf_default_opts(precision=prec, profile=1, hop_variant=args.hop_variant, nsb=args.nsb, schur=schur)
 
     def barrier():
         if dist is not None:
@@ -309,7 +312,7 @@ def run_ours(args):
     # end to end through the host-pointer C ABI call, pinned host buffers
     pin_src = [torch.from_numpy(s).pin_memory().numpy() for s in srcs]
     pin_x = [torch.empty(s.shape, dtype=torch.complex128).pin_memory().numpy() for s in srcs]
-    opts_e2e = M.mdwf_default_opts(precision=prec, hop_variant=args.hop_variant, nsb=args.nsb)
+    opts_e2e = M.mdwf_default_opts(precision=prec, hop_variant=args.hop_variant, nsb=args.nsb, schur=schur)
     M.mdwf_solve_batch(ctx, 0, pin_src, W['tol'], opts=opts_e2e, out=pin_x)
     torch.cuda.synchronize()
     barrier()
@@ -355,6 +358,7 @@ def run_ours(args):
             'config': {'workload': W['name'], 'lattice': '16^3x48', 'L5': W['L5'], 'rhs_per_step': n,
                        'action': {'M5': W['M5'], 'b5': W['b5'], 'c5': W['c5'], 'mf': W['mf']},
                        'gauge': 'exp(i 0.4 H), Wilson flow t=1 (RK3, eps 0.01, FP64)', 'precision': prec,
+                       'schur': args.schur,
                        'l2': 'inputs larger than L2: %.2f GB of inner vectors per step' % (
                            6 * units * BYTES_PER_UNIT[prec] / 1e9),
                        'parallelism': 'replicas' if world > 1 else 'single GPU'},

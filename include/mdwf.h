@@ -80,7 +80,10 @@ typedef struct {
                             multiply (fp16 storage only, else as 1; pipelined through bulk copies
                             when L5 N is a multiple of 8); 4: as 0 with the tensor-core hop among
                             the candidates (its rounding differs from the CUDA-core forms) */
-  int reserved[2];
+  int schur;              /* 0: the asymmetric Schur operator A - D_eo A^-1 D_oe (default, the form
+                            Chroma used, Sec. VII); 1: the symmetric form 1 - A^-1 D_eo A^-1 D_oe the
+                            paper names as the next step (same x; CUDA-core hops only) */
+  int reserved;
 } mdwf_solver_opts;
 
 typedef struct {

@@ -320,6 +320,28 @@ def solve_schur(U, b, M5, b5, c5, mf, tol=1e-10, antiperiodic_t=True, max_iter=1
     return schur_reconstruct(U, b, x_e, M5, b5, c5, mf, antiperiodic_t), iters
 
 
+def schur_op_sym(U, psi_e, M5, b5, c5, mf, antiperiodic_t=True):
+    """Symmetric form Mhat_s = A_ee^-1 Mhat = 1 - A^-1 D_eo A^-1 D_oe (Sec. VII names it as the
+    better-conditioned alternative to the asymmetric form)."""
+    return op_A_inv(schur_op(U, psi_e, M5, b5, c5, mf, antiperiodic_t), M5, b5, c5, mf)
+
+
+def schur_op_sym_dag(U, psi_e, M5, b5, c5, mf, antiperiodic_t=True):
+    """Mhat_s^+ = Mhat^+ A^-+."""
+    return schur_op_dag(U, op_A_inv(psi_e, M5, b5, c5, mf, dagger=True), M5, b5, c5, mf, antiperiodic_t)
+
+
+def solve_schur_sym(U, b, M5, b5, c5, mf, tol=1e-10, antiperiodic_t=True, max_iter=100000):
+    """x = D^-1 b through the symmetric Schur form: CGNR on Mhat_s x_e = A^-1 bhat_e."""
+    bhat = op_A_inv(schur_prepare(U, b, M5, b5, c5, mf, antiperiodic_t), M5, b5, c5, mf)
+    d = 4.0 - M5
+    na = abs(b5 * d + 1.0) + abs(c5 * d - 1.0)
+    x_e, iters = cgnr(lambda v: schur_op_sym(U, v, M5, b5, c5, mf, antiperiodic_t),
+                      lambda v: schur_op_sym_dag(U, v, M5, b5, c5, mf, antiperiodic_t),
+                      bhat, tol / na, max_iter, target_norm=np.sqrt(norm2(b)))
+    return schur_reconstruct(U, b, x_e, M5, b5, c5, mf, antiperiodic_t), iters
+
+
 def true_residual(U, b, x, M5, b5, c5, mf, antiperiodic_t=True):
     """||b - D x|| / ||b|| in FP64."""
     r = b - mobius(U, x, M5, b5, c5, mf, antiperiodic_t)

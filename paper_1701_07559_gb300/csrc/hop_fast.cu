@@ -16,6 +16,9 @@
 //   E_A_SAME     out = add + g A same + kappa H(in)             Mhat, second hop; D; residuals
 //   E_AD_SAME_BD out = add + g A^+ same + kappa B^+ H(in)       Mhat^+, second hop; D^+
 //   E_AINV_SAME  out = A^-1 (same + kappa H(in))                odd-site reconstruction
+//   E_SAME_AINV  out = add + g same + A^-1 (kappa H(in))        symmetric Mhat, second hop
+//   E_SAME_BD    out = add + g same + kappa B^+ H(in)           symmetric Mhat^+, second hop
+//   E_AINVD_SAME out = A^-+ same (no hop)                       symmetric Mhat^+, first pass
 // The recursions run over columns (site, RHS, spin-colour component) of a
 // shared-memory tile that holds every slice of the block's sites.
 //
@@ -352,7 +355,7 @@ template <int L, int EPI, typename T>
 __device__ __forceinline__ void cols_regs(T* base, int st, int s0, const Fifth<T>& f, T m) {
   for (int comp = s0; comp < 24; comp += L) {
     const bool upper = comp < 12;
-    const bool down = (EPI == E_AINVD_BD) ? !upper : upper;
+    const bool down = (EPI == E_AINVD_BD || EPI == E_AINVD_SAME) ? !upper : upper;
     T* p = base + comp + (down ? 0 : (L - 1) * st);
     const int step = down ? st : -st;
     T v[L];
@@ -408,14 +411,17 @@ __device__ __forceinline__ void epilogue(const FastArgs<S, T>& a, const Tiling& 
   const int L5 = a.L5;
   const T m = t.valid ? a.f.mass[t.r] : T(0);
   T o[24];
-  constexpr bool kCols = (EPI == E_BAINV || EPI == E_AINVD_BD || EPI == E_AINV_SAME);
+  constexpr bool kCols = (EPI == E_BAINV || EPI == E_AINVD_BD || EPI == E_AINV_SAME || EPI == E_SAME_AINV ||
+                          EPI == E_AINVD_SAME);
+  constexpr bool kSameFirst = (EPI == E_AINV_SAME || EPI == E_AINVD_SAME);   // same enters before the columns
+  constexpr bool kBdag = (EPI == E_AD_SAME_BD || EPI == E_SAME_BD);
   if (IN_SMEM) __syncthreads();
-  if (kCols || EPI == E_AD_SAME_BD) {
+  if (kCols || kBdag) {
     if (!IN_SMEM) {
       T v[24];
 #pragma unroll
       for (int i = 0; i < 24; i++) v[i] = a.kappa * acc[i];
-      if (EPI == E_AINV_SAME && t.act) {
+      if (kSameFirst && t.act) {
         T y[24];
         load24<S, T>(a.same, a.same_nrm, t.u, y);
 #pragma unroll
@@ -424,7 +430,7 @@ __device__ __forceinline__ void epilogue(const FastArgs<S, T>& a, const Tiling& 
 #pragma unroll
       for (int i = 0; i < 24; i++) sA[t.tid * kPadF + i] = v[i];
       __syncthreads();
-    } else if (EPI == E_AINV_SAME) {
+    } else if (kSameFirst) {
       if (t.act) {
         T y[24];
         load24<S, T>(a.same, a.same_nrm, t.u, y);
@@ -456,6 +462,9 @@ __device__ __forceinline__ void epilogue(const FastArgs<S, T>& a, const Tiling& 
             Col<T> c = make_col<T>(base + comp, st, L5, !upper);
             col_bop<T>(c, L5, a.f.b5, a.f.c5, m);
             col_ainv<T>(c, L5, a.f.inv_alpha, a.f.kap, m, a.f.powL);
+          } else if (EPI == E_AINVD_SAME) {
+            Col<T> c = make_col<T>(base + comp, st, L5, !upper);
+            col_ainv<T>(c, L5, a.f.inv_alpha, a.f.kap, m, a.f.powL);
           } else {
             Col<T> c = make_col<T>(base + comp, st, L5, upper);
             col_ainv<T>(c, L5, a.f.inv_alpha, a.f.kap, m, a.f.powL);
@@ -467,7 +476,7 @@ __device__ __forceinline__ void epilogue(const FastArgs<S, T>& a, const Tiling& 
 #pragma unroll
       for (int i = 0; i < 24; i++) o[i] = sA[t.tid * kPadF + i];
     } else {
-      // E_AD_SAME_BD: B^+ (kappa H) from this slice and its neighbour slice
+      // E_AD_SAME_BD, E_SAME_BD: B^+ (kappa H) from this slice and its neighbour slice
       const int s_dn = t.s == 0 ? L5 - 1 : t.s - 1;
       const int s_up = t.s == L5 - 1 ? 0 : t.s + 1;
       const T w_dn = t.s == 0 ? -m : T(1);
@@ -499,7 +508,14 @@ __device__ __forceinline__ void epilogue(const FastArgs<S, T>& a, const Tiling& 
         for (int i = 0; i < 24; i++) o[i] += a.g_same * y[i];
       }
     }
-    if ((EPI == E_RAW || EPI == E_A_SAME || EPI == E_AD_SAME_BD) && a.add != nullptr) {
+    if ((EPI == E_SAME_AINV || EPI == E_SAME_BD) && a.g_same != T(0)) {
+      T y[24];
+      load24<S, T>(a.same, a.same_nrm, t.u, y);
+#pragma unroll
+      for (int i = 0; i < 24; i++) o[i] += a.g_same * y[i];
+    }
+    if ((EPI == E_RAW || EPI == E_A_SAME || EPI == E_AD_SAME_BD || EPI == E_SAME_AINV || EPI == E_SAME_BD) &&
+        a.add != nullptr) {
       T y[24];
       load24<S, T>(a.add, a.add_nrm, t.u, y);
 #pragma unroll
@@ -554,7 +570,7 @@ __global__ void hop_fast_kernel(FastArgs<S, T> a, Tiling tl) {
   T acc[24];
 #pragma unroll
   for (int i = 0; i < 24; i++) acc[i] = 0;
-  if (t.act) {
+  if (t.act && a.in != nullptr) {      // no input: a local fifth-dimension pass
     const Site x = make_site(a.g, a.out_par, t.h);
     hop_term<0, true, S, T>(a, x, t.h, t.s, t.r, nullptr, 1.f, acc);
     hop_term<0, false, S, T>(a, x, t.h, t.s, t.r, nullptr, 1.f, acc);
@@ -1325,8 +1341,11 @@ size_t staged_smem_bytes(const Tiling& t, int L5, int N) {
 
 template <typename S, typename T>
 cudaError_t launch_fast(const FastArgs<S, T>& a, const Tiling& t, int epi, cudaStream_t st, const StageInfo* stage) {
-  if (stage && (t.rt != a.N || t.ngroups != 1)) stage = nullptr;
+  if (stage && (t.rt != a.N || t.ngroups != 1 || a.in == nullptr)) stage = nullptr;
   switch (epi) {
+    case E_SAME_AINV: return launch_one<S, T, E_SAME_AINV>(a, t, st, stage);
+    case E_SAME_BD: return launch_one<S, T, E_SAME_BD>(a, t, st, stage);
+    case E_AINVD_SAME: return launch_one<S, T, E_AINVD_SAME>(a, t, st, stage);
     case E_RAW: return launch_one<S, T, E_RAW>(a, t, st, stage);
     case E_BAINV: return launch_one<S, T, E_BAINV>(a, t, st, stage);
     case E_AINVD_BD: return launch_one<S, T, E_AINVD_BD>(a, t, st, stage);
@@ -1342,7 +1361,8 @@ int fast_max_threads() {
   int m = max_threads_one<S, T, E_RAW>();
   int v[] = {max_threads_one<S, T, E_BAINV>(), max_threads_one<S, T, E_AINVD_BD>(),
              max_threads_one<S, T, E_A_SAME>(), max_threads_one<S, T, E_AD_SAME_BD>(),
-             max_threads_one<S, T, E_AINV_SAME>()};
+             max_threads_one<S, T, E_AINV_SAME>(), max_threads_one<S, T, E_SAME_AINV>(),
+             max_threads_one<S, T, E_SAME_BD>(), max_threads_one<S, T, E_AINVD_SAME>()};
   for (int x : v) m = x < m ? x : m;
   return m;
 }

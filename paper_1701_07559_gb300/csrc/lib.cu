@@ -468,6 +468,22 @@ struct FastOp {
     if (e != cudaSuccess) return e;
     return run(E_AD_SAME_BD, 0, 1, t, v, none, T(1), T(-0.25), r, active, partials);
   }
+  // Symmetric form Mhat_s = A^-1 Mhat = 1 - 1/4 A^-1 H B A^-1 H B:  q = p + A^-1 (-1/4 H t)
+  cudaError_t mhat_sym(F<S> p, F<S> u, F<S> t, F<S> q, const int* active, double* partials) const {
+    F<S> none;
+    cudaError_t e = run(E_BAINV, 1, 0, u, none, none, T(0), T(1), t, active, nullptr);
+    if (e != cudaSuccess) return e;
+    return run(E_SAME_AINV, 0, 0, t, p, none, T(1), T(-0.25), q, active, partials);
+  }
+  // Mhat_s^+ v = Mhat^+ A^-+ v = v - 1/4 B^+ H^+ A^-+ B^+ H^+ w,  w = A^-+ v ; w, t scratch
+  cudaError_t mhat_sym_dag(F<S> v, F<S> w, F<S> t, F<S> r, const int* active, double* partials) const {
+    F<S> none;
+    cudaError_t e = run(E_AINVD_SAME, 0, 1, none, v, none, T(0), T(0), w, active, nullptr);
+    if (e != cudaSuccess) return e;
+    e = run(E_AINVD_BD, 1, 1, w, none, none, T(0), T(1), t, active, nullptr);
+    if (e != cudaSuccess) return e;
+    return run(E_SAME_BD, 0, 1, t, v, none, T(1), T(-0.25), r, active, partials);
+  }
 };
 
 // Tiling of the fast hop kernels.  Storage types narrower than FP64 stage the
@@ -623,6 +639,7 @@ struct BatchSolver {
   // x_hi before the iterations, bhat and x_hi after them; repacked from the caller's
   // sources, which stay valid for the whole call)
   bool own_b = false;
+  bool sym = false;               // symmetric Schur form (opts.schur == 1)
 
   ~BatchSolver() { if (graph) cudaGraphExecDestroy(graph); }
 
@@ -658,7 +675,10 @@ struct BatchSolver {
     stage.err = errw;
     // the wait-timeout test needs a kernel with waits: the staged one, or the
     // pipelined tensor-core one when that variant is asked for
-    const int variant = o.timeout_test ? (o.hop_variant == HOP_MMA_PIPE ? HOP_MMA_PIPE : HOP_STAGED) : o.hop_variant;
+    sym = o.schur == 1;
+    int variant = o.timeout_test ? (o.hop_variant == HOP_MMA_PIPE ? HOP_MMA_PIPE : HOP_STAGED) : o.hop_variant;
+    // the symmetric form's epilogues exist in the CUDA-core hops only
+    if (sym && (variant == HOP_MMA || variant == HOP_MMA_PIPE || variant == HOP_TUNE_ALL)) variant = HOP_AUTO;
     choose_hop(op64, cf, 0, HOP_DIRECT, &stage);
     choose_hop(op32, cf, nsb, (variant == HOP_AUTO || variant == HOP_TUNE_ALL) ? HOP_DIRECT : variant, &stage);
     choose_hop(opS, cf, nsb, (variant == HOP_AUTO || variant == HOP_TUNE_ALL) ? HOP_DIRECT : variant, &stage);
@@ -793,7 +813,7 @@ struct BatchSolver {
     launches += 8;  // xpay_b, axpy, 3 finalize, 3 scalar kernels (+ 4 hops counted in FastOp::run)
     e = xpay_b<S>(r.v, r.n, p.v, p.n, u.v, u.n, sc.beta, opS.f, tl_blas, g.Vh, L5, N, sc.active, st);
     if (e != cudaSuccess) return e;
-    e = opS.mhat(p, u, t, q, sc.active, part);
+    e = sym ? opS.mhat_sym(p, u, t, q, sc.active, part) : opS.mhat(p, u, t, q, sc.active, part);
     if (e != cudaSuccess) return e;
     e = finalize(part, g.Vh, N, sc.qq, st);
     if (e != cudaSuccess) return e;
@@ -803,7 +823,8 @@ struct BatchSolver {
     e = finalize(part, g.Vh, N, sc.tmp, st);
     if (e != cudaSuccess) return e;
     k_after_rho<<<1, 1024, 0, st>>>(sc, N);
-    e = opS.mhat_dag(rho, t, r, sc.active, part);
+    // (u = B p is dead here: the symmetric form's scratch)
+    e = sym ? opS.mhat_sym_dag(rho, u, t, r, sc.active, part) : opS.mhat_dag(rho, t, r, sc.active, part);
     if (e != cudaSuccess) return e;
     e = finalize(part, g.Vh, N, sc.rr, st);
     if (e != cudaSuccess) return e;
@@ -814,7 +835,7 @@ struct BatchSolver {
   // r = Mhat^+ rho and |r|^2 for the slots in um.
   cudaError_t normal_residual(const int* um) {
     launches += 1;
-    cudaError_t e = opS.mhat_dag(rho, t, r, um, part);
+    cudaError_t e = sym ? opS.mhat_sym_dag(rho, u, t, r, um, part) : opS.mhat_dag(rho, t, r, um, part);
     if (e != cudaSuccess) return e;
     return finalize(part, ctx->g.Vh, N, sc.rr, op64.st);
   }
@@ -831,7 +852,7 @@ struct BatchSolver {
     if (e != cudaSuccess) return e;
     e = bop<float>(xf.v, nullptr, uf.v, nullptr, op32.f, tl_blas, g.Vh, L5, N, um, st);
     if (e != cudaSuccess) return e;
-    e = op32.mhat(xf, uf, tf, qf, um, nullptr);
+    e = sym ? op32.mhat_sym(xf, uf, tf, qf, um, nullptr) : op32.mhat(xf, uf, tf, qf, um, nullptr);
     if (e != cudaSuccess) return e;
     e = resid_update<S>(bhat.v, qf.v, rho.v, rho.n, tl_blas, g.Vh, L5, N, um, part, st);
     if (e != cudaSuccess) return e;
@@ -862,7 +883,8 @@ struct BatchSolver {
       if (e != cudaSuccess) return e;
       e = op64.run(E_BAINV, 1, 0, u64, none, none, 0.0, 1.0, t64, um, nullptr);
       if (e != cudaSuccess) return e;
-      e = op64.run(E_A_SAME, 0, 0, t64, x_hi, bhat, -1.0, 0.25, rho64, um, nullptr);
+      // rho = bhat - Mhat x_hi  (symmetric form: bhat - Mhat_s x_hi)
+      e = op64.run(sym ? E_SAME_AINV : E_A_SAME, 0, 0, t64, x_hi, bhat, -1.0, 0.25, rho64, um, nullptr);
       if (e != cudaSuccess) return e;
     }
     e = norms<double>(rho64, um, sc.tmp);
@@ -920,6 +942,16 @@ struct BatchSolver {
   }
 };
 
+// The symmetric form stops on |A^-1 (bhat - Mhat x)|; since |A| <= alpha + |beta|
+// (A = alpha + beta P with |P| <= 1), stopping at tol / (alpha + |beta|) in that
+// norm keeps the Schur residual, and so the full residual, below tol.
+double sym_stop_factor(const Action& act, const mdwf_solver_opts& o) {
+  if (o.schur != 1) return 1.0;
+  const double d = 4.0 - act.M5;
+  const double na = std::fabs(act.b5 * d + 1.0) + std::fabs(act.c5 * d - 1.0);
+  return 1.0 / (na * na);
+}
+
 int check_cfg(mdwf_ctx* ctx, int cfg_id, Cfg** out) {
   if (!ctx) return MDWF_ERR_ARG;
   auto it = ctx->cfgs.find(cfg_id);
@@ -962,7 +994,7 @@ int solve_batch_impl(mdwf_ctx* ctx, Cfg* cfg, int n, const double* const* srcs, 
   for (int i = 0; i < N; i++) {
     double b2 = bb[i] + bo[i];
     if (!std::isfinite(b2)) return fail(ctx, MDWF_ERR_NONFINITE, "source has NaN/Inf");
-    stop2[i] = 0.25 * tol * tol * b2;
+    stop2[i] = 0.25 * tol * tol * b2 * sym_stop_factor(cfg->act, o);
     if (b2 == 0.0) act[i] = 0;
   }
   CK(cudaMemcpyAsync(sv.sc.stop2, stop2.data(), sizeof(double) * N, cudaMemcpyHostToDevice, st));
@@ -980,6 +1012,10 @@ int solve_batch_impl(mdwf_ctx* ctx, Cfg* cfg, int n, const double* const* srcs, 
     CK(upload_tables_ws<double>(ctx, sv.wsp + "tables", tab, &M, st));
     CK(loc.run(false, 1, 0, sv.b_o, none, M[MK_BAinv], none, nullptr, 0.0, sv.t64, nullptr, nullptr));
     CK(sv.op64.run(E_RAW, 0, 0, sv.t64, none, sv.b_e, 0.0, 0.5, sv.bhat, nullptr, nullptr));
+  }
+  if (sv.sym) {   // symmetric form: the right-hand side A^-1 bhat
+    CK(sv.op64.run(E_AINV_SAME, 0, 0, none, sv.bhat, none, 0.0, 0.0, sv.t64, nullptr, nullptr));
+    CK((convert<double, double>(sv.t64.v, nullptr, sv.bhat.v, nullptr, sv.tl_blas, g.Vh, L5, N, nullptr, st)));
   }
   // x_hi held b_o: the solution starts from zero
   CK(cudaMemsetAsync(sv.x_hi.v, 0, sizeof(double) * 24 * (size_t)g.Vh * L5 * N, st));
@@ -1236,7 +1272,7 @@ struct SessionImpl : SessionBase {
     CK(cudaStreamSynchronize(st));
     b2[r] = be[r] + bo[r];
     if (!std::isfinite(b2[r])) return fail(ctx, MDWF_ERR_NONFINITE, "source has NaN/Inf");
-    const double stop2 = 0.25 * tol * tol * b2[r];
+    const double stop2 = 0.25 * tol * tol * b2[r] * sym_stop_factor(cfg->act, o);
     CK(cudaMemcpyAsync(sv.sc.stop2 + r, &stop2, sizeof(double), cudaMemcpyHostToDevice, st));
     // bhat_e = b_e + 1/2 H_eo B A^-1 b_o on this slot
     {
@@ -1250,6 +1286,10 @@ struct SessionImpl : SessionBase {
       CK(upload_tables_ws<double>(ctx, sv.wsp + "tables", tab, &M, st));
       CK(loc.run(false, 1, 0, sv.b_o, none, M[MK_BAinv], none, nullptr, 0.0, sv.t64, m, nullptr));
       CK(sv.op64.run(E_RAW, 0, 0, sv.t64, none, sv.b_e, 0.0, 0.5, sv.bhat, m, nullptr));
+      if (sv.sym) {
+        CK(sv.op64.run(E_AINV_SAME, 0, 0, none, sv.bhat, none, 0.0, 0.0, sv.t64, m, nullptr));
+        CK((convert<double, double>(sv.t64.v, nullptr, sv.bhat.v, nullptr, sv.tl_blas, g.Vh, L5, N, m, st)));
+      }
     }
     const int one = 1;
     CK(cudaMemcpyAsync(sv.sc.active + r, &one, sizeof(int), cudaMemcpyHostToDevice, st));

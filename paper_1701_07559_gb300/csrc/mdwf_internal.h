@@ -309,7 +309,10 @@ struct HopArgs {
 };
 
 // Structured fifth-dimension epilogues of the fast hop kernel (hop_fast.cu).
-enum Epi { E_RAW = 0, E_BAINV = 1, E_AINVD_BD = 2, E_A_SAME = 3, E_AD_SAME_BD = 4, E_AINV_SAME = 5 };
+enum Epi { E_RAW = 0, E_BAINV = 1, E_AINVD_BD = 2, E_A_SAME = 3, E_AD_SAME_BD = 4, E_AINV_SAME = 5,
+           // symmetric Schur form: add + g same + A^-1 (kappa H in); add + g same + kappa B^+ H in;
+           // A^-+ same (no hop)
+           E_SAME_AINV = 6, E_SAME_BD = 7, E_AINVD_SAME = 8 };
 
 // A = alpha + beta P, B = b5 + c5 P; kap = beta / alpha; mass[r] = m_f of slot r.
 template <typename T>

@@ -45,7 +45,7 @@ class mdwf_solver_opts(ctypes.Structure):
     _fields_ = [('precision', ctypes.c_int), ('max_iter', ctypes.c_int), ('delta', ctypes.c_double),
                 ('chunk', ctypes.c_int), ('use_graph', ctypes.c_int), ('nsb', ctypes.c_int),
                 ('profile', ctypes.c_int), ('wait_timeout_s', ctypes.c_double), ('timeout_test', ctypes.c_int),
-                ('hop_variant', ctypes.c_int), ('reserved', ctypes.c_int * 2)]
+                ('hop_variant', ctypes.c_int), ('schur', ctypes.c_int), ('reserved', ctypes.c_int)]
 
 
 class mdwf_solve_stats(ctypes.Structure):

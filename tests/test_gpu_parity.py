@@ -306,3 +306,52 @@ def test_autotuner_choice_is_cached_and_keeps_results():
             _check_solution(L, b, x, s)
     finally:
         L.close()
+
+
+@pytest.mark.parametrize('precision', ['double', 'single', 'half'])
+def test_symmetric_schur_solve(precision):
+    """The symmetric Schur form (opts.schur = 1) reaches the same solution."""
+    L = Lat(*CASES[0])
+    try:
+        b = np.zeros(L.shape, dtype=np.complex128)
+        b[0, 0, 0, 0, 0, 0, 0] = 1.0
+        x, st = M.mdwf_solve(L.ctx, 0, b, 1e-10, M.mdwf_default_opts(precision=precision, schur=1))
+        _check_solution(L, b, x, st)
+        ref, _ = O.solve_schur(L.U, b, *L.act, tol=1e-13)
+        assert _rel(x, ref) < 1e-8
+    finally:
+        L.close()
+
+
+def test_symmetric_schur_batch_masses_and_session():
+    import torch
+    dims, L5 = (4, 4, 4, 8), 6
+    act = (1.2, 1.25, 0.25, 0.02)
+    U = synth.flowed_gauge(dims, 7, 0.4, flow_t=0.2, flow_eps=0.02)
+    ctx = M.mdwf_create(dims, 0)
+    try:
+        M.mdwf_load_gauge(ctx, 0, U, 1)
+        M.mdwf_set_action(ctx, 0, *act, L5)
+        srcs = [M.mdwf_make_source(ctx, 0, synth.point_source_4d(dims, k // 3, k % 3)) for k in range(6)]
+        masses = [0.02, 0.05, 0.1] * 2
+        opts = M.mdwf_default_opts(precision='half', schur=1)
+        xs, stats = M.mdwf_solve_batch(ctx, 0, srcs, 1e-10, masses=masses, opts=opts)
+        for b, x, st, m in zip(srcs, xs, stats, masses):
+            assert st['converged'] and O.true_residual(U, b, x, act[0], act[1], act[2], m) <= 1e-10
+        sess = M.mdwf_session_create(ctx, 0, 2, 1e-10, opts=opts)
+        try:
+            db = torch.from_numpy(srcs[1]).cuda()
+            dx = torch.empty_like(db)
+            M.mdwf_session_submit(sess, db, 0.05, dx, 1)
+            done = {}
+            for _ in range(500):
+                if M.mdwf_session_occupied(sess) == 0:
+                    break
+                M.mdwf_session_launch(sess)
+                done.update(dict(M.mdwf_session_poll(sess)))
+            assert done[1]['converged']
+            assert O.true_residual(U, srcs[1], dx.cpu().numpy(), act[0], act[1], act[2], 0.05) <= 1e-10
+        finally:
+            M.mdwf_session_destroy(sess)
+    finally:
+        M.mdwf_destroy(ctx)

@@ -507,3 +507,25 @@ def test_gaussian_smearing_covariance_and_width():
         w = sm.sum(axis=tuple(a for a in range(3) if a != axis))
         assert abs(w.sum() - 1.0) < 1e-13
         assert abs((w * c ** 2).sum() - sigma ** 2 / 2) < 1e-12
+
+
+def test_symmetric_schur_form():
+    """The symmetric Schur operator: its adjoint (coded separately) and its
+    solution, which must equal the asymmetric one and the full-lattice one."""
+    dims, L5 = (4, 2, 2, 4), 4
+    act = (1.3, 1.5, 0.5, 0.1)
+    U = synth.random_gauge(dims, 51, 0.5)
+    ev = O.parity_mask(dims)
+    shape = (L5, 4, 2, 2, 4, 4, 3)
+    x = O.restrict(synth.gaussian_spinor(shape, 52), ev)
+    y = O.restrict(synth.gaussian_spinor(shape, 53), ev)
+    lhs = O.vdot(y, O.schur_op_sym(U, x, *act))
+    rhs = O.vdot(O.schur_op_sym_dag(U, y, *act), x)
+    assert abs(lhs - rhs) <= 1e-13 * abs(lhs)
+    b = synth.gaussian_spinor(shape, 54)
+    xs, _ = O.solve_schur_sym(U, b, *act, tol=1e-12)
+    xa, _ = O.solve_schur(U, b, *act, tol=1e-12)
+    xf, _ = O.solve_full(U, b, *act, tol=1e-12)
+    assert np.linalg.norm((xs - xa).ravel()) <= 1e-9 * np.linalg.norm(xa.ravel())
+    assert np.linalg.norm((xs - xf).ravel()) <= 1e-9 * np.linalg.norm(xf.ravel())
+    assert O.true_residual(U, b, xs, *act) <= 1e-12
