@@ -77,9 +77,11 @@ typedef struct {
                             and context and keeps the fastest; all of them give identical results.
                             1: CUDA-core hop with direct neighbour loads; 2: CUDA-core hop with
                             neighbours staged in shared memory by bulk copies; 3: tensor-core colour
-                            multiply (fp16 storage only, else as 1; pipelined through bulk copies
-                            when L5 N is a multiple of 8); 4: as 0 with the tensor-core hop among
-                            the candidates (its rounding differs from the CUDA-core forms) */
+                            multiply (fp16 storage only, else as 1): thread-per-unit loads when the block
+                            is whole warps and L5 x RHS-per-block is a multiple of 8, else 8-unit tiles;
+                            4: as 0 with the tensor-core hop among the candidates (its rounding differs
+                            from the CUDA-core forms); 5: tensor-core tiles double-buffered through bulk
+                            copies (bounded waits) */
   int schur;              /* 0: the asymmetric Schur operator A - D_eo A^-1 D_oe (default, the form
                             Chroma used, Sec. VII); 1: the symmetric form 1 - A^-1 D_eo A^-1 D_oe the
                             paper names as the next step (same x; CUDA-core hops only) */
