@@ -9,7 +9,11 @@ near-identity random SU(3) links smoothed by Wilson flow to t = 1, to a true
 FP64 residual |b - D x| / |b| <= 1e-10.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
-on a bounded sample of the same workload instead.
+on a bounded sample of the same workload instead.  Other modes: ``--mode op``
+applies the batched Schur operator only (a short driver for kernel profiles);
+``--mode serve`` serves a Poisson stream of solve requests over three resident
+configurations and reports p50/p99 latency and solves/s.  ``--schur sym`` solves
+through the symmetric Schur form.
 """
 import argparse
 import json

@@ -10,6 +10,11 @@
 // residual ||b - D x|| after reconstruction.  Inner vectors live in the chosen
 // storage precision (FP32 arithmetic); the solution accumulator x_hi, the
 // residual recomputed at each reliable update, and every global sum are FP64.
+// Options: the symmetric form A^-1 Mhat (opts.schur = 1, the alternative Sec. VII
+// names), the hop form chosen by timing (the autotuner), and solver sessions that
+// keep the CG state of a set of slots resident and admit requests between chunks
+// (continuous batching).  Device workspace is cached per context and reused: no
+// call on the request path allocates or frees device memory once it exists.
 #include <cuda_runtime.h>
 
 #include <chrono>
