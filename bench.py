@@ -50,10 +50,14 @@ def parse():
     ap.add_argument('--lattice', default=None, help="op mode: Lx,Ly,Lz,Lt instead of the workload's 16,16,16,48")
     ap.add_argument('--hop-variant', type=int, default=0,
                     help='0 autotuned (CUDA-core forms), 1 CUDA-core direct loads, 2 CUDA-core staged, '
-                         '3 tensor-core (fp16), 4 autotuned including the tensor-core form')
+                         '3 tensor-core (fp16), 4 autotuned including the staged and tensor-core forms, '
+                         '6 CUDA-core direct, one unit per thread')
     ap.add_argument('--nsb', type=int, default=0, help='sites per thread block (0: chosen by the library)')
     ap.add_argument('--schur', default='asym', choices=['asym', 'sym'],
                     help='Schur form of the solve: asymmetric (default) or symmetric')
+    ap.add_argument('--profile-steps', default='all', choices=['all', 'extra'],
+                    help="'all': the timed solves carry the per-launch hop events and phase timers; "
+                         "'extra': the timed solves run without them and one more solve is profiled")
     ap.add_argument('--requests', type=int, default=300, help='serve mode: requests per arrival rate')
     ap.add_argument('--rates', default='0.5,0.9,1.2', help='serve mode: arrival rates as fractions of capacity')
     ap.add_argument('--serve-lattices', default='16,16,16,48:12;24,24,24,64:8;32,32,32,96:6',
@@ -259,6 +263,8 @@ def run_ours(args):
     dx = [torch.empty_like(s) for s in dsrc]
     schur = 1 if args.schur == 'sym' else 0
     opts = M.mdwf_default_opts(precision=prec, profile=1, hop_variant=args.hop_variant, nsb=args.nsb, schur=schur)
+    opts_timed = opts if args.profile_steps == 'all' else M.mdwf_default_opts(
+        precision=prec, profile=0, hop_variant=args.hop_variant, nsb=args.nsb, schur=schur)
 
     def barrier():
         if dist is not None:
@@ -276,13 +282,16 @@ def run_ours(args):
     t0 = time.perf_counter()
     for i in range(args.steps):
         ev[i][0].record(stream)
-        stats.append(M.mdwf_solve_batch_dev(ctx, 0, dsrc, dx, W['tol'], opts=opts, stream=stream))
+        stats.append(M.mdwf_solve_batch_dev(ctx, 0, dsrc, dx, W['tol'], opts=opts_timed, stream=stream))
         ev[i][1].record(stream)
     torch.cuda.synchronize()
     barrier()
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     clk = clocks.stop()
+    timed = stats
+    if args.profile_steps == 'extra':
+        stats = [M.mdwf_solve_batch_dev(ctx, 0, dsrc, dx, W['tol'], opts=opts, stream=stream)]
     step_ms = [a.elapsed_time(b) for a, b in ev]
     from paper_1701_07559_gb300 import replicas
     # independent replicas: solves of all ranks over the slowest rank's time
@@ -291,7 +300,7 @@ def run_ours(args):
 
     # correctness of what was timed: FP64 true residual of the last step, and the
     # oracle's own D on one solution (rank 0)
-    last = stats[-1]
+    last = timed[-1]
     resid_max = max(s['rel_true_resid'] for s in last)
     assert all(s['converged'] for s in last), last
     iters = [s['iters'] for s in last]
@@ -307,7 +316,7 @@ def run_ours(args):
     achieved = bytes_per_launch / hop_avg_s / 1e9
     peak, peak_kind = measured_peaks()
     gflops = units * 1320 / hop_avg_s / 1e9
-    gpu_launches = sum(s[0]['kernel_launches'] for s in stats)
+    gpu_launches = sum(s[0]['kernel_launches'] for s in timed)
     tuned = M.mdwf_autotune(ctx, 0, n, prec, include_tensor_core=args.hop_variant == 4) \
         if args.hop_variant in (0, 4) and args.nsb == 0 else None
     kernel_name = {1: 'hop_fast_kernel', 2: 'hop_staged_kernel', 3: 'hop_mma_kernel'}.get(
@@ -369,6 +378,12 @@ def run_ours(args):
             'latency_ms': {'p50': statistics.median(step_ms), 'p99': p99, 'per_step': step_ms},
             'iters': iters, 'rel_true_resid_max': resid_max,
             'reliable_updates': [s['reliable_updates'] for s in last],
+            'fp32_updates': [s['fp32_updates'] for s in last],
+            'fp64_rerefs': [s['fp64_rerefs'] for s in last],
+            'phases_ms_per_step': {k: statistics.mean(s[0]['phase_ms'][k] for s in stats)
+                                   for k in M.PHASES},
+            'hop_ms_per_step': hop_ms / len(stats),
+            'profiled_steps': args.profile_steps,
             'fp64_gpu_cg': fp64,
             'speedup_vs_fp64_gpu_cg': (value / fp64['solves_per_s']) if fp64 else None,
             'autotuned': tuned,

@@ -72,16 +72,18 @@ typedef struct {
                             the call with MDWF_ERR_TIMEOUT and leaves the context usable */
   int timeout_test;      /* testing only: 1 makes each staged-copy wait expect bytes that never
                             arrive, so the bound above must end the call with MDWF_ERR_TIMEOUT */
-  int hop_variant;       /* 0: automatic: the autotuner times the CUDA-core hop forms (direct or
-                            staged neighbour loads, 1..8 sites per block) once per (L5, N, precision)
-                            and context and keeps the fastest; all of them give identical results.
-                            1: CUDA-core hop with direct neighbour loads; 2: CUDA-core hop with
+  int hop_variant;       /* 0: automatic: the autotuner times the CUDA-core direct hop with 1..8
+                            sites per block once per (L5, N, precision) and context and keeps the
+                            fastest; all of them give identical results.
+                            1: CUDA-core hop with direct neighbour loads (FP32 arithmetic: two fifth-
+                            dimension slices per thread in packed FP32); 2: CUDA-core hop with
                             neighbours staged in shared memory by bulk copies; 3: tensor-core colour
                             multiply (fp16 storage only, else as 1): thread-per-unit loads when the block
                             is whole warps and L5 x RHS-per-block is a multiple of 8, else 8-unit tiles;
-                            4: as 0 with the tensor-core hop among the candidates (its rounding differs
-                            from the CUDA-core forms); 5: tensor-core tiles double-buffered through bulk
-                            copies (bounded waits) */
+                            4: as 0 with the staged and tensor-core hops among the candidates (their
+                            roundings differ from the direct form); 5: tensor-core tiles double-buffered
+                            through bulk copies (bounded waits); 6: CUDA-core direct hop, one
+                            (site, slice, RHS) unit per thread */
   int schur;              /* 0: the asymmetric Schur operator A - D_eo A^-1 D_oe (default, the form
                             Chroma used, Sec. VII); 1: the symmetric form 1 - A^-1 D_eo A^-1 D_oe the
                             paper names as the next step (same x; CUDA-core hops only) */
@@ -98,6 +100,12 @@ typedef struct {
   double hop_ms;         /* summed device time of those launches (opts.profile), batch total */
   long long kernel_launches; /* kernels this call put on the GPU, batch total */
   long long hop_units;   /* (site, slice, RHS) units per inner hop launch */
+  double phase_ms[5];    /* with opts.profile: device time of the call's phases, batch total:
+                            [0] set-up and Schur preparation (source packing, bhat, first residual),
+                            [1] CG iterations (graph chunks), [2] FP32 reliable updates,
+                            [3] FP64 re-references, [4] reconstruction, FP64 certification, unpacking */
+  int fp32_updates;      /* reliable updates with FP32 arithmetic of this system */
+  int fp64_rerefs;       /* FP64 re-references of this system (the first residual included) */
 } mdwf_solve_stats;
 
 /* Fill opts with the defaults listed above. */

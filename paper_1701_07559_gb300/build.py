@@ -6,7 +6,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, 'csrc')
 BUILD = os.path.join(HERE, '_build')
 LIB = os.path.join(HERE, 'libmdwf.so')
-SOURCES = ['hop.cu', 'hop_fast.cu', 'blas.cu', 'flow.cu', 'lib.cu']
+SOURCES = ['hop.cu', 'hop_fast.cu', 'hop_pair.cu', 'blas.cu', 'flow.cu', 'lib.cu']
 NVCC_FLAGS = ['-gencode', 'arch=compute_103a,code=sm_103a', '-O3', '-lineinfo', '-std=c++17',
               '-Xcompiler', '-fPIC', '-Xcompiler', '-ffp-contract=off']
 

@@ -28,23 +28,36 @@
 // neighbour sites of every site staged into shared memory by bulk asynchronous
 // copies (cp.async.bulk + one mbarrier per direction) issued at block start.
 #include "mdwf_internal.h"
+#include "hop_common.cuh"
 
 namespace mdwf {
 
 namespace {
 
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+// One colour vector times W = l (DAG = false) or l^+ (DAG = true); every real
+// output is one multiply and five fused multiply-adds.
 template <typename T, bool DAG>
 __device__ __forceinline__ void su3_mul(const T* __restrict__ l, const T* v, T* o) {
 #pragma unroll
   for (int a = 0; a < 3; a++) {
-    T re = 0, im = 0;
+    T re, im;
 #pragma unroll
     for (int b = 0; b < 3; b++) {
       const int k = DAG ? (3 * b + a) : (3 * a + b);
       const T ur = l[2 * k];
       const T ui = DAG ? -l[2 * k + 1] : l[2 * k + 1];
-      re += ur * v[2 * b] - ui * v[2 * b + 1];
-      im += ur * v[2 * b + 1] + ui * v[2 * b];
+      if (b == 0) {
+        re = ur * v[0];
+        im = ur * v[1];
+      } else {
+        re = fma_rn(ur, v[2 * b], re);
+        im = fma_rn(ur, v[2 * b + 1], im);
+      }
+      re = fma_rn(-ui, v[2 * b + 1], re);
+      im = fma_rn(ui, v[2 * b], im);
     }
     o[2 * a] = re;
     o[2 * a + 1] = im;
@@ -78,35 +91,6 @@ __device__ __forceinline__ void project(const T* p, T sg, T* h) {
       h0[0] = p0[0] + sg * p2[0]; h0[1] = p0[1] + sg * p2[1];
       h1[0] = p1[0] + sg * p3[0]; h1[1] = p1[1] + sg * p3[1];
     }
-  }
-}
-
-// fp16: project the packed (scaled) values with half2 arithmetic, then unpack and scale.
-template <int MU>
-__device__ __forceinline__ void project_half(const uint4 q[3], float sg, float* h) {
-  const __half2* w = reinterpret_cast<const __half2*>(q);   // w[4 * colour + spin] (colour-major storage)
-  const __half2 pp = __floats2half2_rn(sg, sg);
-  const __half2 mp = __floats2half2_rn(-sg, sg);             // times swapped z: sg * i * z
-#pragma unroll
-  for (int c = 0; c < 3; c++) {
-    const __half2 p0 = w[4 * c], p1 = w[4 * c + 1], p2 = w[4 * c + 2], p3 = w[4 * c + 3];
-    __half2 h0, h1;
-    if (MU == 0) {
-      h0 = __hfma2(__lowhigh2highlow(p3), mp, p0);
-      h1 = __hfma2(__lowhigh2highlow(p2), mp, p1);
-    } else if (MU == 1) {
-      h0 = __hfma2(p3, __hneg2(pp), p0);
-      h1 = __hfma2(p2, pp, p1);
-    } else if (MU == 2) {
-      h0 = __hfma2(__lowhigh2highlow(p2), mp, p0);
-      h1 = __hfma2(__lowhigh2highlow(p3), __hneg2(mp), p1);
-    } else {
-      h0 = __hfma2(p2, pp, p0);
-      h1 = __hfma2(p3, pp, p1);
-    }
-    const float2 f0 = __half22float2(h0), f1 = __half22float2(h1);
-    h[2 * c] = f0.x; h[2 * c + 1] = f0.y;
-    h[6 + 2 * c] = f1.x; h[6 + 2 * c + 1] = f1.y;
   }
 }
 
@@ -179,35 +163,6 @@ __device__ __forceinline__ void reconstruct(const T* chi, T f, T fs, T* acc) {
       a3[0] += fs * x1[0]; a3[1] += fs * x1[1];
     }
   }
-}
-
-// Site of the thread: coordinates, lexicographic index, strides of the four directions.
-struct Site {
-  int c[4];
-  int lex;
-  int stride[4];
-};
-
-__device__ __forceinline__ Site make_site(const Geom& g, int par, long h) {
-  Site x;
-  site_coords(g, par, h, x.c);
-  x.stride[0] = 1;
-  x.stride[1] = g.L[0];
-  x.stride[2] = g.L[0] * g.L[1];
-  x.stride[3] = g.L[0] * g.L[1] * g.L[2];
-  x.lex = x.c[0] + x.stride[1] * x.c[1] + x.stride[2] * x.c[2] + x.stride[3] * x.c[3];
-  return x;
-}
-
-// Half-lattice index of the neighbour in direction MU, forward or backward.
-template <int MU, bool FWD>
-__device__ __forceinline__ int nbr_half(const Geom& g, const Site& x) {
-  const int st = x.stride[MU];
-  const int wrap = (g.L[MU] - 1) * st;
-  int n;
-  if (FWD) n = (x.c[MU] == g.L[MU] - 1) ? x.lex - wrap : x.lex + st;
-  else n = (x.c[MU] == 0) ? x.lex + wrap : x.lex - st;
-  return n >> 1;
 }
 
 // One of the eight hopping terms at neighbour half-site hn (bflip: the term
@@ -1356,6 +1311,9 @@ size_t staged_smem_bytes(const Tiling& t, int L5, int N) {
 template <typename S, typename T>
 cudaError_t launch_fast(const FastArgs<S, T>& a, const Tiling& t, int epi, cudaStream_t st, const StageInfo* stage) {
   if (stage && (t.rt != a.N || t.ngroups != 1 || a.in == nullptr)) stage = nullptr;
+  if constexpr (std::is_same<T, float>::value) {
+    if (stage == nullptr && t.form == 0) return launch_pair<S>(a, t.nsb, epi, st);
+  }
   switch (epi) {
     case E_SAME_AINV: return launch_one<S, T, E_SAME_AINV>(a, t, st, stage);
     case E_SAME_BD: return launch_one<S, T, E_SAME_BD>(a, t, st, stage);

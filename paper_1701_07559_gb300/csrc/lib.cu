@@ -494,8 +494,10 @@ struct FastOp {
 // Tiling of the fast hop kernels.  Storage types narrower than FP64 stage the
 // neighbour sites in shared memory when a block can hold whole sites (all N
 // slots of nsb sites, at most ~200 KB of staging); FP64 runs unstaged.
-// Hop kernel variants: 0 automatic, 1 CUDA-core direct loads, 2 CUDA-core staged, 3 tensor-core (fp16).
-enum { HOP_AUTO = 0, HOP_DIRECT = 1, HOP_STAGED = 2, HOP_MMA = 3, HOP_TUNE_ALL = 4, HOP_MMA_PIPE = 5 };
+// Hop kernel variants: 0 automatic, 1 CUDA-core direct loads (two slices per thread for FP32
+// arithmetic), 2 CUDA-core staged, 3 tensor-core (fp16), 6 CUDA-core direct, one unit per thread.
+enum { HOP_AUTO = 0, HOP_DIRECT = 1, HOP_STAGED = 2, HOP_MMA = 3, HOP_TUNE_ALL = 4, HOP_MMA_PIPE = 5,
+       HOP_UNIT = 6 };
 
 template <typename S>
 Tiling fast_tiling(const Geom& g, int L5, int N, int nsb_req, bool* staged, bool allow_staging);
@@ -525,6 +527,7 @@ void choose_hop(FastOp<S, T>& op, const Cfg* cfg, int nsb_req, int variant, cons
     if (mma_hop_usable(op.tl, L5, N)) { op.mma = true; op.stage = stage; return; }
   }
   op.tl = fast_tiling<S>(g, L5, N, nsb_req, &staged, variant == HOP_STAGED);
+  op.tl.form = variant == HOP_UNIT ? 1 : 0;
   op.stage = staged ? stage : nullptr;
 }
 
@@ -548,6 +551,10 @@ Tiling fast_tiling(const Geom& g, int L5, int N, int nsb_req, bool* staged, bool
   if (smem_thr < maxthr) maxthr = smem_thr;
   int nsb = nsb_req > 0 ? nsb_req : 2;
   if (nsb > 64) nsb = 64;
+  // by default keep every RHS slot of a site in one block (no ragged slot groups,
+  // whose idle lanes cost the FP64 hop 40 % of its time when 2 sites did not fit)
+  if (nsb_req <= 0)
+    while (nsb > 1 && nsb * L5 * N > maxthr) nsb--;
   return make_tiling(g.Vh, L5, N, nsb, maxthr);
 }
 
@@ -741,9 +748,9 @@ struct BatchSolver {
   // Autotuner: time Mhat + Mhat^+ of the inner precision over the candidate hop
   // forms and block shapes on this solver's own fields, keep the fastest, and
   // remember it in the context for (L5, N, precision, candidate set).  HOP_AUTO
-  // tries only forms with the same arithmetic (CUDA-core hop, direct or staged
-  // neighbours, 1..8 sites per block), so the choice never changes a result;
-  // HOP_TUNE_ALL adds the tensor-core hop.
+  // tries only forms with the same arithmetic (the CUDA-core direct hop with
+  // 1..8 sites per block), so the choice never changes a result; HOP_TUNE_ALL
+  // adds the staged and tensor-core hops, whose roundings differ.
   int tune(int which, int* variant_out = nullptr, int* nsb_out = nullptr, double* ms_out = nullptr) {
     mdwf_ctx* ctx = this->ctx;
     const int prec = kFP64 ? MDWF_PREC_DOUBLE : std::is_same<S, float>::value ? MDWF_PREC_SINGLE
@@ -754,7 +761,7 @@ struct BatchSolver {
       std::vector<std::array<int, 2>> cand;
       for (int nsbc : {1, 2, 4, 8})
         if (nsbc * L5 <= 1024) cand.push_back({HOP_DIRECT, nsbc});
-      if (!kFP64) cand.push_back({HOP_STAGED, 0});
+      if (which == HOP_TUNE_ALL && !kFP64) cand.push_back({HOP_STAGED, 0});
       if (which == HOP_TUNE_ALL && std::is_same<S, __half>::value) cand.push_back({HOP_MMA, 0});
       cudaStream_t st = op64.st;
       cudaEvent_t e0, e1;
@@ -968,12 +975,46 @@ int check_cfg(mdwf_ctx* ctx, int cfg_id, Cfg** out) {
 
 cudaStream_t pick_stream(mdwf_ctx* ctx, void* s) { return s ? (cudaStream_t)s : ctx->stream; }
 
+// Device time of the phases of a solve (opts.profile): an event pair per phase
+// interval, read after the synchronisation that ends it.
+struct Phases {
+  bool on = false;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  double ms[5] = {0, 0, 0, 0, 0};
+  cudaError_t begin(bool enable, cudaStream_t st) {
+    on = enable;
+    if (!on) return cudaSuccess;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+    return e;
+  }
+  // close the current interval as phase k and open the next one
+  cudaError_t mark(int k, cudaStream_t st) {
+    if (!on) return cudaSuccess;
+    cudaError_t e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    ms[k] += t;
+    std::swap(e0, e1);
+    return e;
+  }
+  ~Phases() {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  }
+};
+enum { PH_PREP = 0, PH_CG = 1, PH_UPD32 = 2, PH_REREF = 3, PH_FINAL = 4 };
+
 // Solve on device API-layout buffers.
 template <typename S>
 int solve_batch_impl(mdwf_ctx* ctx, Cfg* cfg, int n, const double* const* srcs, const std::vector<double>& masses,
                      double* const* xs, double tol, const mdwf_solver_opts& o, mdwf_solve_stats* stats,
                      cudaStream_t st) {
   auto t0 = std::chrono::steady_clock::now();
+  Phases ph;
+  CK(ph.begin(o.profile != 0, st));
   BatchSolver<S> sv;
   int rc = sv.init(ctx, cfg, masses, o.nsb, o.profile != 0, o, st);
   if (rc != MDWF_OK) return rc;
@@ -1030,7 +1071,8 @@ int solve_batch_impl(mdwf_ctx* ctx, Cfg* cfg, int n, const double* const* srcs, 
   CK(cudaMemcpyAsync(sv.sc.active, act.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(sv.umask_d, um.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
   CK(sv.reref(sv.umask_d, true));
-  std::vector<int> flags(N), iters(N), nupd(N, 1), done(N, 0);
+  CK(ph.mark(PH_PREP, st));
+  std::vector<int> flags(N), iters(N), nupd(N, 1), done(N, 0), n32(N, 0), n64(N, 1);
   for (int i = 0; i < N; i++) if (!act[i]) done[i] = 1;
   const int chunk = o.chunk > 0 ? o.chunk : 16;
   auto read_flags = [&]() -> int {
@@ -1053,6 +1095,7 @@ int solve_batch_impl(mdwf_ctx* ctx, Cfg* cfg, int n, const double* const* srcs, 
     rc = sv.run_chunk(chunk, o.use_graph != 0);
     if (rc != MDWF_OK) return rc;
     if ((rc = read_flags())) return rc;
+    CK(ph.mark(PH_CG, st));
     CK(sv.collect(o.use_graph != 0));
     // reliable updates: FP32 arithmetic (mixed) or FP64 (FP64 solver)
     bool any = false;
@@ -1065,8 +1108,9 @@ int solve_batch_impl(mdwf_ctx* ctx, Cfg* cfg, int n, const double* const* srcs, 
       if (BatchSolver<S>::kFP64) CK(sv.reref(sv.umask_d, false));
       else CK(sv.update32(sv.umask_d));
       if ((rc = read_flags())) return rc;
+      CK(ph.mark(BatchSolver<S>::kFP64 ? PH_REREF : PH_UPD32, st));
       CK(sv.collect(false));
-      for (int i = 0; i < N; i++) if (um[i]) nupd[i]++;
+      for (int i = 0; i < N; i++) if (um[i]) { nupd[i]++; (BatchSolver<S>::kFP64 ? n64 : n32)[i]++; }
     }
     // FP64 re-references requested by the FP32 updates
     any = false;
@@ -1078,8 +1122,9 @@ int solve_batch_impl(mdwf_ctx* ctx, Cfg* cfg, int n, const double* const* srcs, 
       CK(cudaMemcpyAsync(sv.umask_d, um.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
       CK(sv.reref(sv.umask_d, false));
       if ((rc = read_flags())) return rc;
+      CK(ph.mark(PH_REREF, st));
       CK(sv.collect(false));
-      for (int i = 0; i < N; i++) if (um[i]) nupd[i]++;
+      for (int i = 0; i < N; i++) if (um[i]) { nupd[i]++; n64[i]++; }
     }
     bool stop_any = false;
     for (int i = 0; i < N; i++) {
@@ -1093,6 +1138,7 @@ int solve_batch_impl(mdwf_ctx* ctx, Cfg* cfg, int n, const double* const* srcs, 
       for (int i = 0; i < N; i++) if (done[i]) a[i] = 0;
       CK(cudaMemcpyAsync(sv.sc.active, a.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
     }
+    CK(ph.mark(PH_CG, st));   // (host bookkeeping between chunks)
   }
   // x_e = x_acc + x_hi + x_lo
   sv.launches += 2 + 2 * N;
@@ -1125,6 +1171,7 @@ int solve_batch_impl(mdwf_ctx* ctx, Cfg* cfg, int n, const double* const* srcs, 
     CK(unpack_rhs<double>(sv.x_o.v, nullptr, xs[i], g, L5, N, 1, i, st));
   }
   CK(cudaStreamSynchronize(st));
+  CK(ph.mark(PH_FINAL, st));
   double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   int status = MDWF_OK;
   for (int i = 0; i < N; i++) {
@@ -1142,6 +1189,9 @@ int solve_batch_impl(mdwf_ctx* ctx, Cfg* cfg, int n, const double* const* srcs, 
       stats[i].hop_ms = sv.prof.ms;
       stats[i].kernel_launches = sv.launches;
       stats[i].hop_units = (long long)g.Vh * L5 * N;
+      for (int k = 0; k < 5; k++) stats[i].phase_ms[k] = ph.ms[k];
+      stats[i].fp32_updates = n32[i];
+      stats[i].fp64_rerefs = n64[i];
     }
   }
   if (status != MDWF_OK) fail(ctx, status, "solve did not reach the tolerance within max_iter");

@@ -5,7 +5,8 @@
 //                                                 dimension slice, r = RHS slot,
 //                                                 24 = [spin 4][colour 3][re, im]
 //   16-bit storage adds a scale per (h, s, r):   nrm[h][s][r] (float); the stored
-//                                                 values are v / nrm, nrm = max |v|.
+//                                                 values are v / nrm, nrm = the smallest power
+//                                                 of two >= max |v| of the unit.
 //   fp16 storage orders the 24 reals of a unit colour-major, [colour][spin][re,im],
 //   so that the four spins of one colour are one 16-byte word (the tensor-core hop
 //   loads them per lane); every other type, and every register copy, uses
@@ -106,6 +107,28 @@ __device__ __forceinline__ void load24<__nv_bfloat16, float>(const __nv_bfloat16
   }
 }
 
+// Scale of an fp16-stored unit whose largest |component| is m: the smallest
+// power of two >= m.  Its reciprocal is exact, so each stored value is rounded
+// once (to fp16), and the largest lies in [1/2, 1].  A unit whose largest entry
+// is below the smallest normal float is stored as zero; above 2^126 the scale is
+// m itself.
+__device__ __forceinline__ void half_scale(float m, float* sc, float* inv) {
+  *sc = 0.f;
+  *inv = 0.f;
+  if (m >= 1.17549435e-38f) {
+    const unsigned mb = __float_as_uint(m);
+    unsigned e = mb & 0x7f800000u;
+    if (mb & 0x007fffffu) e += 0x00800000u;
+    if (e <= (253u << 23)) {
+      *sc = __uint_as_float(e);
+      *inv = __uint_as_float(0x7f000000u - e);
+    } else {
+      *sc = m;
+      *inv = 1.0f / m;
+    }
+  }
+}
+
 // Store the 24 reals of unit u.
 template <typename S, typename T>
 __device__ __forceinline__ void store24(S* __restrict__ v, float* __restrict__ nrm, long u, const T a[24]);
@@ -127,11 +150,9 @@ __device__ __forceinline__ void store24<__half, float>(__half* __restrict__ v, f
   float m = 0.f;
 #pragma unroll
   for (int i = 0; i < 24; i++) m = fmaxf(m, fabsf(a[i]));
-  // A unit whose largest entry is below the smallest normal float is stored as
-  // zero (its reciprocal would overflow); such entries are < 1e-38 of O(1) data.
-  float inv = m >= 1.17549435e-38f ? 1.0f / m : 0.f;
-  if (inv == 0.f) m = 0.f;
-  nrm[u] = m;
+  float sc, inv;
+  half_scale(m, &sc, &inv);
+  nrm[u] = sc;
   uint4* p = reinterpret_cast<uint4*>(v + 24 * u);
 #pragma unroll
   for (int c = 0; c < 3; c++) {
@@ -271,6 +292,7 @@ struct Tiling {
   long ntiles; // ceil(Vh / nsb)
   int ngroups; // ceil(N / rt)
   int threads; // nsb * L5 * rt
+  int form = 0; // FP32-arithmetic direct hop: 0 two slices per thread (hop_pair.cu), 1 one unit per thread
 };
 
 inline Tiling make_tiling(long Vh, int L5, int N, int nsb, int max_threads = 1024) {
@@ -353,6 +375,14 @@ struct StageInfo {
 template <typename S, typename T>
 cudaError_t launch_fast(const FastArgs<S, T>& a, const Tiling& t, int epi, cudaStream_t st,
                         const StageInfo* stage = nullptr);
+// Two-slices-per-thread hop (hop_pair.cu): block (rt, J = ceil(L5 / 2), nsb).
+struct PairShape {
+  int J, nsb, rt, threads;
+  size_t smem;
+};
+PairShape pair_shape(int L5, int N, int nsb);
+template <typename S>
+cudaError_t launch_pair(const FastArgs<S, float>& a, int nsb, int epi, cudaStream_t st);
 // Tensor-core hop (fp16 storage): usable when a block holds whole sites and L5 N % 8 == 0.
 bool mma_hop_usable(const Tiling& t, int L5, int N);
 int mma_max_threads();

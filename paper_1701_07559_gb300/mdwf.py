@@ -48,16 +48,23 @@ class mdwf_solver_opts(ctypes.Structure):
                 ('hop_variant', ctypes.c_int), ('schur', ctypes.c_int), ('reserved', ctypes.c_int)]
 
 
+# the phases of mdwf_solve_stats.phase_ms
+PHASES = ('prep', 'cg', 'fp32_update', 'fp64_reref', 'final')
+
+
 class mdwf_solve_stats(ctypes.Structure):
     _fields_ = [('iters', ctypes.c_int), ('reliable_updates', ctypes.c_int), ('converged', ctypes.c_int),
                 ('hop_launches', ctypes.c_int), ('rel_true_resid', ctypes.c_double), ('time_s', ctypes.c_double),
                 ('hop_ms', ctypes.c_double), ('kernel_launches', ctypes.c_longlong),
-                ('hop_units', ctypes.c_longlong)]
+                ('hop_units', ctypes.c_longlong), ('phase_ms', ctypes.c_double * 5),
+                ('fp32_updates', ctypes.c_int), ('fp64_rerefs', ctypes.c_int)]
 
     def as_dict(self):
         return {'iters': self.iters, 'reliable_updates': self.reliable_updates, 'converged': bool(self.converged),
                 'rel_true_resid': self.rel_true_resid, 'time_s': self.time_s, 'hop_launches': self.hop_launches,
-                'hop_ms': self.hop_ms, 'kernel_launches': self.kernel_launches, 'hop_units': self.hop_units}
+                'hop_ms': self.hop_ms, 'kernel_launches': self.kernel_launches, 'hop_units': self.hop_units,
+                'phase_ms': dict(zip(PHASES, list(self.phase_ms))), 'fp32_updates': self.fp32_updates,
+                'fp64_rerefs': self.fp64_rerefs}
 
 
 class MdwfError(RuntimeError):
@@ -316,7 +323,7 @@ def mdwf_solve_batch_dev(ctx, cfg_id, srcs, xs, tol, masses=None, opts=None, str
     return [s.as_dict() for s in st]
 
 
-HOP_AUTO, HOP_DIRECT, HOP_STAGED, HOP_MMA, HOP_TUNE_ALL = 0, 1, 2, 3, 4
+HOP_AUTO, HOP_DIRECT, HOP_STAGED, HOP_MMA, HOP_TUNE_ALL, HOP_MMA_PIPE, HOP_UNIT = 0, 1, 2, 3, 4, 5, 6
 
 
 def mdwf_apply_schur_batch_dev(ctx, cfg_id, ins, outs, masses=None, dagger=0, precision=MDWF_PREC_HALF,
