@@ -87,7 +87,10 @@ typedef struct {
   int schur;              /* 0: the asymmetric Schur operator A - D_eo A^-1 D_oe (default, the form
                             Chroma used, Sec. VII); 1: the symmetric form 1 - A^-1 D_eo A^-1 D_oe the
                             paper names as the next step (same x; CUDA-core hops only) */
-  int reserved;
+  int max_restarts;       /* a system whose FP64 full-lattice certificate misses tol resumes from its x
+                            with a 16 times tighter Schur stopping norm, at most this often (default 3) */
+  double stop_scale_test; /* testing only: multiplies the Schur stopping norm (default 1); above 1 the
+                            first certificate misses tol, so the restarts above must finish the solve */
 } mdwf_solver_opts;
 
 typedef struct {
@@ -106,6 +109,7 @@ typedef struct {
                             [3] FP64 re-references, [4] reconstruction, FP64 certification, unpacking */
   int fp32_updates;      /* reliable updates with FP32 arithmetic of this system */
   int fp64_rerefs;       /* FP64 re-references of this system (the first residual included) */
+  int restarts;          /* resumptions after a missed certificate (opts.max_restarts), batch total */
 } mdwf_solve_stats;
 
 /* Fill opts with the defaults listed above. */
@@ -215,8 +219,10 @@ int mdwf_apply_schur_batch_dev(mdwf_ctx* ctx, int cfg_id, int n, const double* c
  * larger problem is rejected with MDWF_ERR_ARG and a message giving the size.
  *
  * The first call on a device looks up the array's device address (with that
- * device current) and caches it; make that first call before any stream
- * capture.  Every call uses the same array, which keeps the previous call's
+ * device current) and caches it for the life of the process; make that first
+ * call before any stream capture.  A device reset (cudaDeviceReset) makes the
+ * cached address stale: do not use this entry point after one.  Every call
+ * uses the same array, which keeps the previous call's
  * contents (the kernels overwrite what they read, and the one field that must
  * start at zero is cleared by the call itself); calls that overlap on the GPU --
  * from several streams or host threads at once -- race on the array and must be

@@ -346,15 +346,22 @@ Tiling tiling_for(const Geom& g, int L5, int N, int nsb, bool two_buffers) {
 struct Scal {
   double *gamma, *gamma_prev, *alpha, *beta, *rho2, *rho2_max, *stop2, *qq, *rr, *tmp, *bhat2, *upd2;
   int *active, *flags, *iters;
+  int* since;     // CG iterations since the last reliable update of the slot
+  int stag_max;   // that many without one: the inner recursion stagnates (see k_after_rho)
   double delta2;  // periodic reliable update when |rho|^2 < delta2 * max |rho|^2 since the last one
   double tau2;    // FP64 re-reference when |rho|^2 <= tau2 * |bhat|^2 (bhat = current reference residual)
 };
-enum { FLAG_INNER_DONE = 1, FLAG_UPDATE = 2, FLAG_DONE = 4, FLAG_REREF = 8 };
+enum { FLAG_INNER_DONE = 1, FLAG_UPDATE = 2, FLAG_DONE = 4, FLAG_REREF = 8, FLAG_STAG = 16 };
 
 __global__ void k_alpha(Scal c, int N) {
   int r = threadIdx.x;
   if (r < N && c.active[r]) { double q = c.qq[r]; c.alpha[r] = q > 0.0 ? c.gamma[r] / q : 0.0; }
 }
+// The low-precision residual recursion can stagnate for a system whose
+// residual is already tiny: it neither reaches the stopping norm nor drops by
+// delta, so no update would ever come.  After stag_max iterations without an
+// update one is forced; it is followed by an FP64 re-reference and a restart of
+// the search direction (beta = 0).
 __global__ void k_after_rho(Scal c, int N) {
   int r = threadIdx.x;
   if (r < N && c.active[r]) {
@@ -363,6 +370,7 @@ __global__ void k_after_rho(Scal c, int N) {
     if (v > c.rho2_max[r]) c.rho2_max[r] = v;
     if (v <= c.stop2[r]) { c.active[r] = 0; c.flags[r] |= FLAG_INNER_DONE; }
     else if (v < c.delta2 * c.rho2_max[r] || v <= c.tau2 * c.bhat2[r]) c.flags[r] |= FLAG_UPDATE;
+    else if (c.since[r] >= c.stag_max) c.flags[r] |= FLAG_UPDATE | FLAG_STAG;
   }
 }
 __global__ void k_beta(Scal c, int N) {
@@ -373,6 +381,7 @@ __global__ void k_beta(Scal c, int N) {
     c.gamma_prev[r] = g;
     c.gamma[r] = rr;
     c.iters[r] += 1;
+    c.since[r] += 1;
   }
 }
 // After a residual recomputed with FP32 arithmetic.  Its error grows like
@@ -394,10 +403,14 @@ __global__ void k_after_update(Scal c, int N, const int* um) {
     c.gamma[r] = c.rr[r];
     c.beta[r] = c.gamma_prev[r] > 0.0 ? c.gamma[r] / c.gamma_prev[r] : 0.0;
     const bool fine = c.bhat2[r] <= 1e6 * c.stop2[r];
-    const bool stalled = prev > 0.0 && v > 0.25 * prev;
+    const bool stag = (c.flags[r] & FLAG_STAG) != 0;
+    const bool stalled = stag || (prev > 0.0 && v > 0.25 * prev);
+    c.since[r] = 0;
     if (v <= c.stop2[r] && fine) { c.flags[r] = FLAG_DONE; c.active[r] = 0; }
-    else if (v <= c.stop2[r] || v <= c.tau2 * c.bhat2[r] || stalled) { c.flags[r] = FLAG_REREF; c.active[r] = 1; }
-    else { c.flags[r] = 0; c.active[r] = 1; }
+    else if (v <= c.stop2[r] || v <= c.tau2 * c.bhat2[r] || stalled) {
+      c.flags[r] = FLAG_REREF | (stag ? FLAG_STAG : 0);
+      c.active[r] = 1;
+    } else { c.flags[r] = 0; c.active[r] = 1; }
   }
 }
 // After an FP64 re-reference (bhat <- rho, x_acc += x_hi).
@@ -410,7 +423,9 @@ __global__ void k_after_reref(Scal c, int N, const int* um) {
     c.bhat2[r] = v;
     c.upd2[r] = 0.0;
     c.gamma[r] = c.rr[r];
-    c.beta[r] = c.gamma_prev[r] > 0.0 ? c.gamma[r] / c.gamma_prev[r] : 0.0;
+    // after a stagnation the search direction restarts from the new residual
+    c.beta[r] = (c.gamma_prev[r] > 0.0 && !(c.flags[r] & FLAG_STAG)) ? c.gamma[r] / c.gamma_prev[r] : 0.0;
+    c.since[r] = 0;
     if (v <= c.stop2[r]) { c.flags[r] = FLAG_DONE; c.active[r] = 0; }
     else { c.flags[r] = 0; c.active[r] = 1; }
   }
@@ -720,15 +735,16 @@ struct BatchSolver {
     CK(ws_field<SX>(c, wsp + "xlo", units, &xlo));
     part = (double*)ws_get(c, wsp + "partials", sizeof(double) * g.Vh * N, &e); CK(e);
     double* d = (double*)ws_get(c, wsp + "scal_d", sizeof(double) * 12 * N, &e); CK(e);
-    int* ip = (int*)ws_get(c, wsp + "scal_i", sizeof(int) * 3 * N, &e); CK(e);
+    int* ip = (int*)ws_get(c, wsp + "scal_i", sizeof(int) * 4 * N, &e); CK(e);
     umask_d = (int*)ws_get(c, wsp + "umask", sizeof(int) * N, &e); CK(e);
     sc.gamma = d; sc.gamma_prev = d + N; sc.alpha = d + 2 * N; sc.beta = d + 3 * N; sc.rho2 = d + 4 * N;
     sc.rho2_max = d + 5 * N; sc.stop2 = d + 6 * N; sc.qq = d + 7 * N; sc.rr = d + 8 * N; sc.tmp = d + 9 * N;
     sc.bhat2 = d + 10 * N;
     sc.upd2 = d + 11 * N;
-    sc.active = ip; sc.flags = ip + N; sc.iters = ip + 2 * N;
+    sc.active = ip; sc.flags = ip + N; sc.iters = ip + 2 * N; sc.since = ip + 3 * N;
+    sc.stag_max = 128;
     CK(cudaMemsetAsync(d, 0, sizeof(double) * 12 * N, st));
-    CK(cudaMemsetAsync(ip, 0, sizeof(int) * 3 * N, st));
+    CK(cudaMemsetAsync(ip, 0, sizeof(int) * 4 * N, st));
     const size_t b64 = sizeof(double) * 24 * (size_t)units;
     CK(cudaMemsetAsync(x_acc.v, 0, b64, st));
     CK(cudaMemsetAsync(x_hi.v, 0, b64, st));
@@ -1007,7 +1023,11 @@ struct Phases {
 };
 enum { PH_PREP = 0, PH_CG = 1, PH_UPD32 = 2, PH_REREF = 3, PH_FINAL = 4 };
 
-// Solve on device API-layout buffers.
+// Solve on device API-layout buffers.  After the CG loop every system's x is
+// reconstructed and certified by its FP64 full-lattice residual |b - D x| / |b|;
+// a system whose certificate misses tol (while it has iterations left) resumes
+// from its x with a 16 times tighter Schur stopping norm, up to opts.max_restarts
+// times (the restart of reading 7).
 template <typename S>
 int solve_batch_impl(mdwf_ctx* ctx, Cfg* cfg, int n, const double* const* srcs, const std::vector<double>& masses,
                      double* const* xs, double tol, const mdwf_solver_opts& o, mdwf_solve_stats* stats,
@@ -1020,34 +1040,31 @@ int solve_batch_impl(mdwf_ctx* ctx, Cfg* cfg, int n, const double* const* srcs, 
   if (rc != MDWF_OK) return rc;
   const Geom& g = ctx->g;
   const int N = n, L5 = cfg->act.L5;
+  const size_t field_bytes = sizeof(double) * 24 * (size_t)g.Vh * L5 * N;
   F<double> none;
-  sv.launches += 2 * N;
-  sv.b_e = sv.rho64;
-  sv.b_o = sv.x_hi;
-  for (int i = 0; i < N; i++) {
-    CK(pack_rhs<double>(srcs[i], sv.b_e.v, nullptr, g, L5, N, 0, i, st));
-    CK(pack_rhs<double>(srcs[i], sv.b_o.v, nullptr, g, L5, N, 1, i, st));
-  }
-  std::vector<double> bb(N), bo(N);
   double* tmp = sv.sc.tmp;
-  CK(sv.norms(sv.b_e, nullptr, tmp));
-  CK(cudaMemcpyAsync(bb.data(), tmp, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
-  CK(sv.norms(sv.b_o, nullptr, tmp));
-  CK(cudaMemcpyAsync(bo.data(), tmp, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
-  std::vector<double> stop2(N);
-  std::vector<int> act(N, 1);
-  for (int i = 0; i < N; i++) {
-    double b2 = bb[i] + bo[i];
-    if (!std::isfinite(b2)) return fail(ctx, MDWF_ERR_NONFINITE, "source has NaN/Inf");
-    stop2[i] = 0.25 * tol * tol * b2 * sym_stop_factor(cfg->act, o);
-    if (b2 == 0.0) act[i] = 0;
-  }
-  CK(cudaMemcpyAsync(sv.sc.stop2, stop2.data(), sizeof(double) * N, cudaMemcpyHostToDevice, st));
-  sv.sc.delta2 = BatchSolver<S>::kFP64 ? 0.0 : o.delta * o.delta;
-  sv.sc.tau2 = BatchSolver<S>::kFP64 ? 0.0 : 1e-10;
-  // bhat_e = b_e + 1/2 H_eo B A^-1 b_o   (B A^-1 on the odd sites with the dense table kernel)
-  {
+  std::vector<double> bb(N), bo(N), stop2(N);
+  std::vector<int> act(N, 1), um(N), flags(N), iters(N), nupd(N, 1), done(N, 0), n32(N, 0), n64(N, 1);
+  std::vector<int> cap(N, o.max_iter);   // iteration limit of each system (a restart gets a budget)
+  int restarts = 0;
+
+  // Schur right-hand side bhat_e = b_e + 1/2 H_eo B A^-1 b_o in bhat (FP64); the
+  // sources are packed into rho64 (b_e) and x_hi (b_o), which are free then.
+  auto schur_source = [&](bool norms) -> int {
+    sv.launches += 2 * N;
+    sv.b_e = sv.rho64;
+    sv.b_o = sv.x_hi;
+    for (int i = 0; i < N; i++) {
+      CK(pack_rhs<double>(srcs[i], sv.b_e.v, nullptr, g, L5, N, 0, i, st));
+      CK(pack_rhs<double>(srcs[i], sv.b_o.v, nullptr, g, L5, N, 1, i, st));
+    }
+    if (norms) {
+      CK(sv.norms(sv.b_e, nullptr, tmp));
+      CK(cudaMemcpyAsync(bb.data(), tmp, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
+      CK(sv.norms(sv.b_o, nullptr, tmp));
+      CK(cudaMemcpyAsync(bo.data(), tmp, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+    }
     Op<double, double> loc;
     loc.g = g; loc.L5 = L5; loc.N = N; loc.anti = cfg->anti; loc.U = cfg->U64; loc.st = st;
     loc.tl = tiling_for<double>(g, L5, N, sv.op64.tl.nsb, true);
@@ -1058,21 +1075,31 @@ int solve_batch_impl(mdwf_ctx* ctx, Cfg* cfg, int n, const double* const* srcs, 
     CK(upload_tables_ws<double>(ctx, sv.wsp + "tables", tab, &M, st));
     CK(loc.run(false, 1, 0, sv.b_o, none, M[MK_BAinv], none, nullptr, 0.0, sv.t64, nullptr, nullptr));
     CK(sv.op64.run(E_RAW, 0, 0, sv.t64, none, sv.b_e, 0.0, 0.5, sv.bhat, nullptr, nullptr));
+    if (sv.sym) {   // symmetric form: the right-hand side A^-1 bhat
+      CK(sv.op64.run(E_AINV_SAME, 0, 0, none, sv.bhat, none, 0.0, 0.0, sv.t64, nullptr, nullptr));
+      CK((convert<double, double>(sv.t64.v, nullptr, sv.bhat.v, nullptr, sv.tl_blas, g.Vh, L5, N, nullptr, st)));
+    }
+    // x_hi held b_o
+    CK(cudaMemsetAsync(sv.x_hi.v, 0, field_bytes, st));
+    return MDWF_OK;
+  };
+
+  if ((rc = schur_source(true))) return rc;
+  for (int i = 0; i < N; i++) {
+    double b2 = bb[i] + bo[i];
+    if (!std::isfinite(b2)) return fail(ctx, MDWF_ERR_NONFINITE, "source has NaN/Inf");
+    stop2[i] = 0.25 * tol * tol * b2 * sym_stop_factor(cfg->act, o) * o.stop_scale_test * o.stop_scale_test;
+    if (b2 == 0.0) act[i] = 0;
   }
-  if (sv.sym) {   // symmetric form: the right-hand side A^-1 bhat
-    CK(sv.op64.run(E_AINV_SAME, 0, 0, none, sv.bhat, none, 0.0, 0.0, sv.t64, nullptr, nullptr));
-    CK((convert<double, double>(sv.t64.v, nullptr, sv.bhat.v, nullptr, sv.tl_blas, g.Vh, L5, N, nullptr, st)));
-  }
-  // x_hi held b_o: the solution starts from zero
-  CK(cudaMemsetAsync(sv.x_hi.v, 0, sizeof(double) * 24 * (size_t)g.Vh * L5 * N, st));
+  CK(cudaMemcpyAsync(sv.sc.stop2, stop2.data(), sizeof(double) * N, cudaMemcpyHostToDevice, st));
+  sv.sc.delta2 = BatchSolver<S>::kFP64 ? 0.0 : o.delta * o.delta;
+  sv.sc.tau2 = BatchSolver<S>::kFP64 ? 0.0 : 1e-10;
   // initial residual (x = 0)
-  std::vector<int> um(N);
   for (int i = 0; i < N; i++) um[i] = act[i];
   CK(cudaMemcpyAsync(sv.sc.active, act.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(sv.umask_d, um.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
   CK(sv.reref(sv.umask_d, true));
   CK(ph.mark(PH_PREP, st));
-  std::vector<int> flags(N), iters(N), nupd(N, 1), done(N, 0), n32(N, 0), n64(N, 1);
   for (int i = 0; i < N; i++) if (!act[i]) done[i] = 1;
   const int chunk = o.chunk > 0 ? o.chunk : 16;
   auto read_flags = [&]() -> int {
@@ -1088,95 +1115,141 @@ int solve_batch_impl(mdwf_ctx* ctx, Cfg* cfg, int n, const double* const* srcs, 
     }
     return MDWF_OK;
   };
+
+  // CG chunks with reliable updates until every system is done
+  auto iterate = [&]() -> int {
+    int rc2;
+    for (;;) {
+      bool all = true;
+      for (int i = 0; i < N; i++) all = all && done[i];
+      if (all) break;
+      rc2 = sv.run_chunk(chunk, o.use_graph != 0);
+      if (rc2 != MDWF_OK) return rc2;
+      if ((rc2 = read_flags())) return rc2;
+      CK(ph.mark(PH_CG, st));
+      CK(sv.collect(o.use_graph != 0));
+      // reliable updates: FP32 arithmetic (mixed) or FP64 (FP64 solver)
+      bool any = false;
+      for (int i = 0; i < N; i++) {
+        um[i] = (!done[i] && (flags[i] & (FLAG_INNER_DONE | FLAG_UPDATE))) ? 1 : 0;
+        any = any || um[i];
+      }
+      if (any) {
+        CK(cudaMemcpyAsync(sv.umask_d, um.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
+        if (BatchSolver<S>::kFP64) CK(sv.reref(sv.umask_d, false));
+        else CK(sv.update32(sv.umask_d));
+        if ((rc2 = read_flags())) return rc2;
+        CK(ph.mark(BatchSolver<S>::kFP64 ? PH_REREF : PH_UPD32, st));
+        CK(sv.collect(false));
+        for (int i = 0; i < N; i++) if (um[i]) { nupd[i]++; (BatchSolver<S>::kFP64 ? n64 : n32)[i]++; }
+      }
+      // FP64 re-references requested by the FP32 updates
+      any = false;
+      for (int i = 0; i < N; i++) {
+        um[i] = (!done[i] && (flags[i] & FLAG_REREF)) ? 1 : 0;
+        any = any || um[i];
+      }
+      if (any) {
+        CK(cudaMemcpyAsync(sv.umask_d, um.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
+        CK(sv.reref(sv.umask_d, false));
+        if ((rc2 = read_flags())) return rc2;
+        CK(ph.mark(PH_REREF, st));
+        CK(sv.collect(false));
+        for (int i = 0; i < N; i++) if (um[i]) { nupd[i]++; n64[i]++; }
+      }
+      bool stop_any = false;
+      for (int i = 0; i < N; i++) {
+        if (flags[i] & FLAG_DONE) done[i] = 1;
+        if (!done[i] && iters[i] >= cap[i]) { done[i] = 1; stop_any = true; }
+      }
+      if (stop_any) {
+        std::vector<int> a(N);
+        CK(cudaMemcpyAsync(a.data(), sv.sc.active, sizeof(int) * N, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        for (int i = 0; i < N; i++) if (done[i]) a[i] = 0;
+        CK(cudaMemcpyAsync(sv.sc.active, a.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
+      }
+      CK(ph.mark(PH_CG, st));   // (host bookkeeping between chunks)
+    }
+    return MDWF_OK;
+  };
+
+  // x_e = x_acc (+ x_hi + x_lo), reconstruction, FP64 certificate on both
+  // parities, unpacking into xs.  Odd sites: y = b_o + 1/2 H_oe B x_e (one FP64
+  // hop), x_o = A^-1 y, and the odd residual b_o - A x_o + 1/2 H_oe B x_e = y - A x_o
+  // reuses y.  Even sites: b_e - A x_e + 1/2 H_eo B x_o (the second FP64 hop).
+  std::vector<double> re(N), ro(N);
+  auto finish = [&]() -> int {
+    sv.launches += 2 + 2 * N;
+    CK(accum_xhi<typename BatchSolver<S>::SX>(sv.x_hi.v, sv.xlo.v, sv.tl_blas, g.Vh, L5, N, nullptr, st));
+    CK(accum_xhi<double>(sv.x_acc.v, sv.x_hi.v, sv.tl_blas, g.Vh, L5, N, nullptr, st));
+    // sources again, in fields now free (bhat, x_hi)
+    sv.b_e = sv.bhat;
+    sv.b_o = sv.x_hi;
+    for (int i = 0; i < N; i++) {
+      CK(pack_rhs<double>(srcs[i], sv.b_e.v, nullptr, g, L5, N, 0, i, st));
+      CK(pack_rhs<double>(srcs[i], sv.b_o.v, nullptr, g, L5, N, 1, i, st));
+    }
+    sv.launches += 2;
+    CK(bop<double>(sv.x_acc.v, nullptr, sv.u64.v, nullptr, sv.op64.f, sv.tl_blas, g.Vh, L5, N, nullptr, st));
+    CK(sv.op64.run(E_RAW, 1, 0, sv.u64, none, sv.b_o, 0.0, 0.5, sv.t64, nullptr, nullptr));
+    CK(sv.op64.run(E_AINV_SAME, 1, 0, none, sv.t64, none, 0.0, 0.0, sv.x_o, nullptr, nullptr));
+    CK(sv.op64.run(E_A_SAME, 1, 0, none, sv.x_o, sv.t64, -1.0, 0.0, sv.rho64, nullptr, nullptr));
+    CK(sv.norms(sv.rho64, nullptr, tmp));
+    CK(cudaMemcpyAsync(ro.data(), tmp, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
+    CK(bop<double>(sv.x_o.v, nullptr, sv.u64.v, nullptr, sv.op64.f, sv.tl_blas, g.Vh, L5, N, nullptr, st));
+    CK(sv.op64.run(E_A_SAME, 0, 0, sv.u64, sv.x_acc, sv.b_e, -1.0, 0.5, sv.rho64, nullptr, nullptr));
+    CK(sv.norms(sv.rho64, nullptr, tmp));
+    CK(cudaMemcpyAsync(re.data(), tmp, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(iters.data(), sv.sc.iters, sizeof(int) * N, cudaMemcpyDeviceToHost, st));
+    for (int i = 0; i < N; i++) {
+      CK(unpack_rhs<double>(sv.x_acc.v, nullptr, xs[i], g, L5, N, 0, i, st));
+      CK(unpack_rhs<double>(sv.x_o.v, nullptr, xs[i], g, L5, N, 1, i, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    CK(ph.mark(PH_FINAL, st));
+    return MDWF_OK;
+  };
+  auto rel_of = [&](int i) {
+    const double b2 = bb[i] + bo[i];
+    return b2 > 0 ? std::sqrt((re[i] + ro[i]) / b2) : 0.0;
+  };
+
   for (;;) {
-    bool all = true;
-    for (int i = 0; i < N; i++) all = all && done[i];
-    if (all) break;
-    rc = sv.run_chunk(chunk, o.use_graph != 0);
-    if (rc != MDWF_OK) return rc;
-    if ((rc = read_flags())) return rc;
-    CK(ph.mark(PH_CG, st));
-    CK(sv.collect(o.use_graph != 0));
-    // reliable updates: FP32 arithmetic (mixed) or FP64 (FP64 solver)
+    if ((rc = iterate())) return rc;
+    if ((rc = finish())) return rc;
     bool any = false;
     for (int i = 0; i < N; i++) {
-      um[i] = (!done[i] && (flags[i] & (FLAG_INNER_DONE | FLAG_UPDATE))) ? 1 : 0;
+      um[i] = (act[i] && rel_of(i) > tol && iters[i] < o.max_iter) ? 1 : 0;
       any = any || um[i];
     }
-    if (any) {
-      CK(cudaMemcpyAsync(sv.umask_d, um.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
-      if (BatchSolver<S>::kFP64) CK(sv.reref(sv.umask_d, false));
-      else CK(sv.update32(sv.umask_d));
-      if ((rc = read_flags())) return rc;
-      CK(ph.mark(BatchSolver<S>::kFP64 ? PH_REREF : PH_UPD32, st));
-      CK(sv.collect(false));
-      for (int i = 0; i < N; i++) if (um[i]) { nupd[i]++; (BatchSolver<S>::kFP64 ? n64 : n32)[i]++; }
-    }
-    // FP64 re-references requested by the FP32 updates
-    any = false;
-    for (int i = 0; i < N; i++) {
-      um[i] = (!done[i] && (flags[i] & FLAG_REREF)) ? 1 : 0;
-      any = any || um[i];
-    }
-    if (any) {
-      CK(cudaMemcpyAsync(sv.umask_d, um.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
-      CK(sv.reref(sv.umask_d, false));
-      if ((rc = read_flags())) return rc;
-      CK(ph.mark(PH_REREF, st));
-      CK(sv.collect(false));
-      for (int i = 0; i < N; i++) if (um[i]) { nupd[i]++; n64[i]++; }
-    }
-    bool stop_any = false;
-    for (int i = 0; i < N; i++) {
-      if (flags[i] & FLAG_DONE) done[i] = 1;
-      if (!done[i] && iters[i] >= o.max_iter) { done[i] = 1; stop_any = true; }
-    }
-    if (stop_any) {
-      std::vector<int> a(N);
-      CK(cudaMemcpyAsync(a.data(), sv.sc.active, sizeof(int) * N, cudaMemcpyDeviceToHost, st));
-      CK(cudaStreamSynchronize(st));
-      for (int i = 0; i < N; i++) if (done[i]) a[i] = 0;
-      CK(cudaMemcpyAsync(sv.sc.active, a.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
-    }
-    CK(ph.mark(PH_CG, st));   // (host bookkeeping between chunks)
+    if (!any || restarts >= o.max_restarts) break;
+    // resume the systems that missed tol from their x: bhat is rebuilt from the
+    // sources, x_acc moves into x_hi for those systems, and an FP64 re-reference
+    // forms bhat - Mhat x_hi with a 16 times tighter stopping norm
+    restarts++;
+    if ((rc = schur_source(false))) return rc;
+    CK(cudaMemcpyAsync(sv.umask_d, um.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
+    sv.launches += 1;
+    CK(accum_xhi<double>(sv.x_hi.v, sv.x_acc.v, sv.tl_blas, g.Vh, L5, N, sv.umask_d, st));
+    // each resumed system gets a budget of a quarter of the iterations it has
+    // used (at least 64): a tighter norm below what its FP64 residual can
+    // resolve then ends in NOT_CONVERGED with its certificate, not at max_iter
+    for (int i = 0; i < N; i++)
+      if (um[i]) {
+        stop2[i] /= 256.0;
+        done[i] = 0;
+        cap[i] = (int)std::min<long long>(o.max_iter, (long long)iters[i] + std::max(64, iters[i] / 4));
+      }
+    CK(cudaMemcpyAsync(sv.sc.stop2, stop2.data(), sizeof(double) * N, cudaMemcpyHostToDevice, st));
+    CK(sv.reref(sv.umask_d, false));
+    for (int i = 0; i < N; i++) if (um[i]) { nupd[i]++; n64[i]++; }
+    CK(ph.mark(PH_REREF, st));
   }
-  // x_e = x_acc + x_hi + x_lo
-  sv.launches += 2 + 2 * N;
-  CK(accum_xhi<typename BatchSolver<S>::SX>(sv.x_hi.v, sv.xlo.v, sv.tl_blas, g.Vh, L5, N, nullptr, st));
-  CK(accum_xhi<double>(sv.x_acc.v, sv.x_hi.v, sv.tl_blas, g.Vh, L5, N, nullptr, st));
-  // sources again, in fields now free (bhat, x_hi)
-  sv.b_e = sv.bhat;
-  sv.b_o = sv.x_hi;
-  sv.launches += 2 * N;
-  for (int i = 0; i < N; i++) {
-    CK(pack_rhs<double>(srcs[i], sv.b_e.v, nullptr, g, L5, N, 0, i, st));
-    CK(pack_rhs<double>(srcs[i], sv.b_o.v, nullptr, g, L5, N, 1, i, st));
-  }
-  // x_o = A^-1 (b_o + 1/2 H_oe B x_e)
-  sv.launches += 2;
-  CK(bop<double>(sv.x_acc.v, nullptr, sv.u64.v, nullptr, sv.op64.f, sv.tl_blas, g.Vh, L5, N, nullptr, st));
-  CK(sv.op64.run(E_AINV_SAME, 1, 0, sv.u64, sv.b_o, none, 0.0, 0.5, sv.x_o, nullptr, nullptr));
-  // true residual b - D x = b - A x + 1/2 H B x on both parities
-  CK(bop<double>(sv.x_o.v, nullptr, sv.t64.v, nullptr, sv.op64.f, sv.tl_blas, g.Vh, L5, N, nullptr, st));
-  CK(sv.op64.run(E_A_SAME, 0, 0, sv.t64, sv.x_acc, sv.b_e, -1.0, 0.5, sv.rho64, nullptr, nullptr));
-  std::vector<double> re(N), ro(N);
-  CK(sv.norms(sv.rho64, nullptr, tmp));
-  CK(cudaMemcpyAsync(re.data(), tmp, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
-  CK(sv.op64.run(E_A_SAME, 1, 0, sv.u64, sv.x_o, sv.b_o, -1.0, 0.5, sv.rho64, nullptr, nullptr));
-  CK(sv.norms(sv.rho64, nullptr, tmp));
-  CK(cudaMemcpyAsync(ro.data(), tmp, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(iters.data(), sv.sc.iters, sizeof(int) * N, cudaMemcpyDeviceToHost, st));
-  for (int i = 0; i < N; i++) {
-    CK(unpack_rhs<double>(sv.x_acc.v, nullptr, xs[i], g, L5, N, 0, i, st));
-    CK(unpack_rhs<double>(sv.x_o.v, nullptr, xs[i], g, L5, N, 1, i, st));
-  }
-  CK(cudaStreamSynchronize(st));
-  CK(ph.mark(PH_FINAL, st));
   double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   int status = MDWF_OK;
   for (int i = 0; i < N; i++) {
-    double b2 = bb[i] + bo[i];
-    double rel = b2 > 0 ? std::sqrt((re[i] + ro[i]) / b2) : 0.0;
+    const double rel = rel_of(i);
     bool conv = rel <= tol;
     if (!conv) status = MDWF_ERR_NOT_CONVERGED;
     if (stats) {
@@ -1192,6 +1265,7 @@ int solve_batch_impl(mdwf_ctx* ctx, Cfg* cfg, int n, const double* const* srcs, 
       for (int k = 0; k < 5; k++) stats[i].phase_ms[k] = ph.ms[k];
       stats[i].fp32_updates = n32[i];
       stats[i].fp64_rerefs = n64[i];
+      stats[i].restarts = restarts;
     }
   }
   if (status != MDWF_OK) fail(ctx, status, "solve did not reach the tolerance within max_iter");
@@ -1306,7 +1380,7 @@ struct SessionImpl : SessionBase {
     // fresh per-slot state
     const int zi = 0;
     const double zd = 0.0;
-    int* ia[] = {sv.sc.active, sv.sc.flags, sv.sc.iters};
+    int* ia[] = {sv.sc.active, sv.sc.flags, sv.sc.iters, sv.sc.since};
     for (int* a : ia) CK(cudaMemcpyAsync(a + r, &zi, sizeof(int), cudaMemcpyHostToDevice, st));
     double* da[] = {sv.sc.gamma, sv.sc.gamma_prev, sv.sc.alpha, sv.sc.beta, sv.sc.rho2, sv.sc.rho2_max, sv.sc.qq,
                     sv.sc.rr, sv.sc.tmp, sv.sc.bhat2, sv.sc.upd2};
@@ -1709,6 +1783,8 @@ void mdwf_default_opts(mdwf_solver_opts* o) {
   o->nsb = 0;
   o->wait_timeout_s = 2.0;
   o->hop_variant = 0;
+  o->max_restarts = 3;
+  o->stop_scale_test = 1.0;
 }
 
 int mdwf_create(const int dims[4], int device, mdwf_ctx** out) {
@@ -1855,20 +1931,25 @@ int mdwf_solve_batch(mdwf_ctx* ctx, int cfg_id, int n, const double* const* srcs
   int rc = check_cfg(ctx, cfg_id, &cfg);
   if (rc) return rc;
   if (n < 1 || n > 1024 || !srcs || !xs) return fail(ctx, MDWF_ERR_ARG, "solve_batch: bad n or pointers");
+  for (int i = 0; i < n; i++)
+    if (!srcs[i] || !xs[i]) return fail(ctx, MDWF_ERR_ARG, "solve_batch: null source or solution");
   CK(cudaSetDevice(ctx->device));
   cudaStream_t st = ctx->stream;
   const size_t n5 = (size_t)cfg->act.L5 * ctx->g.V * 24;
-  DBuf dsrc, dx;
-  CK(dsrc.alloc(sizeof(double) * n5 * n));
-  CK(dx.alloc(sizeof(double) * n5 * n));
+  // device copies of the sources and solutions live in the context's workspace
+  // (allocated once, grown on demand); a non-finite source is caught by the
+  // solve's own device norms (MDWF_ERR_NONFINITE), so the host does not scan it
+  cudaError_t e = cudaSuccess;
+  double* dsrc = (double*)ws_get(ctx, "e2e.src", sizeof(double) * n5 * n, &e);
+  CK(e);
+  double* dx = (double*)ws_get(ctx, "e2e.x", sizeof(double) * n5 * n, &e);
+  CK(e);
   std::vector<const double*> s(n);
   std::vector<double*> x(n);
   for (int i = 0; i < n; i++) {
-    if (!srcs[i] || !xs[i]) return fail(ctx, MDWF_ERR_ARG, "solve_batch: null source or solution");
-    if (!all_finite(srcs[i], n5)) return fail(ctx, MDWF_ERR_NONFINITE, "source has NaN/Inf");
-    CK(cudaMemcpyAsync(dsrc.as<double>() + n5 * i, srcs[i], sizeof(double) * n5, cudaMemcpyHostToDevice, st));
-    s[i] = dsrc.as<double>() + n5 * i;
-    x[i] = dx.as<double>() + n5 * i;
+    CK(cudaMemcpyAsync(dsrc + n5 * i, srcs[i], sizeof(double) * n5, cudaMemcpyHostToDevice, st));
+    s[i] = dsrc + n5 * i;
+    x[i] = dx + n5 * i;
   }
   rc = solve_dispatch(ctx, cfg_id, n, s.data(), masses, x.data(), tol, opts, stats, st);
   if (rc != MDWF_OK && rc != MDWF_ERR_NOT_CONVERGED) return rc;

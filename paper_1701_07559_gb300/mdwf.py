@@ -45,7 +45,8 @@ class mdwf_solver_opts(ctypes.Structure):
     _fields_ = [('precision', ctypes.c_int), ('max_iter', ctypes.c_int), ('delta', ctypes.c_double),
                 ('chunk', ctypes.c_int), ('use_graph', ctypes.c_int), ('nsb', ctypes.c_int),
                 ('profile', ctypes.c_int), ('wait_timeout_s', ctypes.c_double), ('timeout_test', ctypes.c_int),
-                ('hop_variant', ctypes.c_int), ('schur', ctypes.c_int), ('reserved', ctypes.c_int)]
+                ('hop_variant', ctypes.c_int), ('schur', ctypes.c_int), ('max_restarts', ctypes.c_int),
+                ('stop_scale_test', ctypes.c_double)]
 
 
 # the phases of mdwf_solve_stats.phase_ms
@@ -57,14 +58,14 @@ class mdwf_solve_stats(ctypes.Structure):
                 ('hop_launches', ctypes.c_int), ('rel_true_resid', ctypes.c_double), ('time_s', ctypes.c_double),
                 ('hop_ms', ctypes.c_double), ('kernel_launches', ctypes.c_longlong),
                 ('hop_units', ctypes.c_longlong), ('phase_ms', ctypes.c_double * 5),
-                ('fp32_updates', ctypes.c_int), ('fp64_rerefs', ctypes.c_int)]
+                ('fp32_updates', ctypes.c_int), ('fp64_rerefs', ctypes.c_int), ('restarts', ctypes.c_int)]
 
     def as_dict(self):
         return {'iters': self.iters, 'reliable_updates': self.reliable_updates, 'converged': bool(self.converged),
                 'rel_true_resid': self.rel_true_resid, 'time_s': self.time_s, 'hop_launches': self.hop_launches,
                 'hop_ms': self.hop_ms, 'kernel_launches': self.kernel_launches, 'hop_units': self.hop_units,
                 'phase_ms': dict(zip(PHASES, list(self.phase_ms))), 'fp32_updates': self.fp32_updates,
-                'fp64_rerefs': self.fp64_rerefs}
+                'fp64_rerefs': self.fp64_rerefs, 'restarts': self.restarts}
 
 
 class MdwfError(RuntimeError):
@@ -333,6 +334,10 @@ def mdwf_apply_schur_batch_dev(ctx, cfg_id, ins, outs, masses=None, dagger=0, pr
         precision = PRECISIONS[precision]
     shape = _shape5(ctx, cfg_id)
     n = len(ins)
+    if len(outs) != n:
+        raise ValueError('mdwf_apply_schur_batch_dev: %d inputs but %d outputs' % (n, len(outs)))
+    if masses is not None and len(masses) != n:
+        raise ValueError('mdwf_apply_schur_batch_dev: %d inputs but %d masses' % (n, len(masses)))
     ip = (_P * n)(*[_dev_ptr(t, shape) for t in ins])
     op = (_P * n)(*[_dev_ptr(t, shape) for t in outs])
     m = None
@@ -355,6 +360,10 @@ def mdwf_apply_schur_batch_dev_noalloc(ctx, cfg_id, ins, outs, masses=None, dagg
         precision = PRECISIONS[precision]
     shape = _shape5(ctx, cfg_id)
     n = len(ins)
+    if len(outs) != n:
+        raise ValueError('mdwf_apply_schur_batch_dev_noalloc: %d inputs but %d outputs' % (n, len(outs)))
+    if masses is not None and len(masses) != n:
+        raise ValueError('mdwf_apply_schur_batch_dev_noalloc: %d inputs but %d masses' % (n, len(masses)))
     ip = (_P * n)(*[_dev_ptr(t, shape) for t in ins])
     op = (_P * n)(*[_dev_ptr(t, shape) for t in outs])
     m = None

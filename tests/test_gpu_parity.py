@@ -1,7 +1,8 @@
 """GPU parity: every step of the hot path, called through the C ABI, against the
 FP64 CPU oracle on the same seeded inputs.
 
-Tolerances (norm-wise relative, ||gpu - oracle|| / ||oracle||):
+Tolerances (norm-wise relative, ||gpu - oracle|| / ||oracle||, and element by
+element, max |gpu - oracle| <= C u max |oracle| with u the storage unit roundoff):
   FP64 operator applies                     1e-13
   FP32 storage/arithmetic Schur operator   2e-6   (a few float roundings per term)
   fp16 storage (scaled), FP32 arithmetic   4e-3   (2^-11 rounding of each stored field)
@@ -30,6 +31,26 @@ def setup_module(module):
 
 def _rel(a, b):
     return np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel())
+
+
+# Element-wise bound: max |gpu - oracle| <= C * u * max |oracle|, with u the unit
+# roundoff of the storage type (FP64, FP32, fp16, bf16).  C counts the roundings
+# that reach one component through the operator: the stored input, the stored
+# intermediate odd field, the stored output (each u relative to its unit's
+# largest component) and the FP32 products and sums of the 8 hopping terms, of
+# A^-1 and of B.  Measured worst cases over every hop form, dagger, L5 and mass
+# of these tests: C = 2.7 (FP64), 2.4 (FP32), 1.3 (fp16), 1.3 (bf16); the bound
+# C = 16 keeps a margin of at least 6.  A single wrong component
+# (a dropped term, a wrong sign) is of the size of max |oracle| itself, 1/u
+# times larger than u, so it cannot pass.
+UNIT = {'double': 2.0 ** -53, 'single': 2.0 ** -24, 'half': 2.0 ** -11, 'bf16': 2.0 ** -8}
+CELEM = {'double': 16.0, 'single': 16.0, 'half': 16.0, 'bf16': 16.0}
+
+
+def _check_elementwise(out, ref, precision):
+    err = np.abs(out - ref).max()
+    bound = CELEM[precision] * UNIT[precision] * np.abs(ref).max()
+    assert err <= bound, 'max |gpu - oracle| = %.3g > %.3g (%s)' % (err, bound, precision)
 
 
 # (dims, L5, action, gauge seed/eps): several tiles, ragged tails (Vh*L5 not a
@@ -72,6 +93,7 @@ def test_dslash_fp64(lat, out_parity, dagger):
         mask = O.parity_mask(lat.dims)
         ref = O.restrict(ref, mask if out_parity == 0 else 1 - mask)
     assert _rel(out, ref) < 1e-13
+    _check_elementwise(out, ref, 'double')
 
 
 @pytest.mark.parametrize('dagger', [0, 1])
@@ -79,7 +101,9 @@ def test_mdwf_fp64(lat, dagger):
     psi = synth.gaussian_spinor(lat.shape, 12)
     out = M.mdwf_apply_mdwf(lat.ctx, 0, psi, dagger)
     f = O.mobius_dag if dagger else O.mobius
-    assert _rel(out, f(lat.U, psi, *lat.act)) < 1e-13
+    ref = f(lat.U, psi, *lat.act)
+    assert _rel(out, ref) < 1e-13
+    _check_elementwise(out, ref, 'double')
 
 
 @pytest.mark.parametrize('op', ['A', 'B', 'Ainv'])
@@ -92,6 +116,7 @@ def test_fifth_dimension_ops(lat, op, dagger):
            'B': lambda v: O.op_B(v, b5, c5, mf, bool(dagger)),
            'Ainv': lambda v: O.op_A_inv(v, M5, b5, c5, mf, bool(dagger))}[op](psi)
     assert _rel(out, ref) < 1e-13
+    _check_elementwise(out, ref, 'double')
 
 
 @pytest.mark.parametrize('precision,tol', [('double', 1e-13), ('single', 2e-6), ('half', 4e-3), ('bf16', 3e-2)])
@@ -101,14 +126,18 @@ def test_schur_operator(lat, precision, tol, dagger):
     psi = O.restrict(synth.gaussian_spinor(lat.shape, 14), ev)
     out = M.mdwf_apply_schur(lat.ctx, 0, psi, dagger, precision)
     f = O.schur_op_dag if dagger else O.schur_op
-    assert _rel(out, f(lat.U, psi, *lat.act)) < tol
+    ref = f(lat.U, psi, *lat.act)
+    assert _rel(out, ref) < tol
+    _check_elementwise(out, ref, precision)
 
 
 def test_make_source(lat):
     eta = synth.gaussian_spinor(tuple(reversed(lat.dims)) + (4, 3), 15)
     out = M.mdwf_make_source(lat.ctx, 0, eta)
     M5, b5, c5, mf = lat.act
-    assert _rel(out, O.make_source(lat.U, eta, M5, c5, lat.L5)) < 1e-13
+    ref = O.make_source(lat.U, eta, M5, c5, lat.L5)
+    assert _rel(out, ref) < 1e-13
+    _check_elementwise(out, ref, 'double')
 
 
 def test_time_boundary_periodic_option():
@@ -120,7 +149,9 @@ def test_time_boundary_periodic_option():
         M.mdwf_set_action(ctx, 0, 1.3, 1.5, 0.5, 0.1, L5)
         psi = synth.gaussian_spinor((L5, 4, 2, 2, 4, 4, 3), 16)
         out = M.mdwf_apply_dslash(ctx, 0, psi, -1, 0)
-        assert _rel(out, O.hopping(U, psi, False)) < 1e-13
+        ref = O.hopping(U, psi, False)
+        assert _rel(out, ref) < 1e-13
+        _check_elementwise(out, ref, 'double')
     finally:
         M.mdwf_destroy(ctx)
 
@@ -253,15 +284,22 @@ def test_bounded_wait_reports_timeout_and_context_survives(variant):
         L.close()
 
 
+# the production tiling: N = 12, two sites per block (what the autotuner picks for
+# the 16^3 x 48, L5 = 12 workload), at the L5 of every workload (8, 12) and 16
+MASSES12 = [0.0022, 0.0102, 0.0126, 0.0158, 0.0216, 0.05, 0.1, 0.2, 0.3, 0.01, 0.02, 0.07]
+
+
 @pytest.mark.parametrize('precision,tol', [('double', 1e-13), ('single', 2e-6), ('half', 4e-3), ('bf16', 3e-2)])
 @pytest.mark.parametrize('dagger', [0, 1])
-@pytest.mark.parametrize('variant', [0, 1, 2, 3, 5])
+@pytest.mark.parametrize('variant', [0, 1, 2, 3, 5, 6, 1 | (2 << 8), 6 | (2 << 8)])
 @pytest.mark.parametrize('L5,masses', [(5, [0.05, 0.01, 0.2, 0.0022, 0.1]),            # L5 N = 25
                                        (4, [0.05, 0.01, 0.2, 0.0022]),                 # L5 N = 16: tensor-core tiles
-                                       (6, [0.05, 0.01, 0.2, 0.0022, 0.1, 0.3, 0.02, 0.07])])   # L5 N = 48
+                                       (6, [0.05, 0.01, 0.2, 0.0022, 0.1, 0.3, 0.02, 0.07]),   # L5 N = 48
+                                       (8, MASSES12), (12, MASSES12), (16, MASSES12)])
 def test_schur_batch_multi_rhs(precision, tol, dagger, variant, L5, masses):
     """The batched Schur operator (the solver's kernels, N RHS with different masses,
-    every hop variant) against the oracle, slot by slot."""
+    every hop variant; bits 8..15 of the variant fix the sites per block) against
+    the oracle, slot by slot, norm-wise and element by element."""
     import torch
     dims = (6, 4, 4, 6)
     act = (1.2, 1.25, 0.25, 0.05)
@@ -280,7 +318,9 @@ def test_schur_batch_multi_rhs(precision, tol, dagger, variant, L5, masses):
         f = O.schur_op_dag if dagger else O.schur_op
         for x, o, m in zip(xs, outs, masses):
             ref = f(U, x, act[0], act[1], act[2], m)
-            assert _rel(o.cpu().numpy(), ref) < tol
+            o = o.cpu().numpy()
+            assert _rel(o, ref) < tol
+            _check_elementwise(o, ref, precision)
     finally:
         M.mdwf_destroy(ctx)
 
@@ -304,6 +344,30 @@ def test_autotuner_choice_is_cached_and_keeps_results():
             assert np.array_equal(x, y)
         for b, x, s in zip(bs, xa, sa):
             _check_solution(L, b, x, s)
+    finally:
+        L.close()
+
+
+@pytest.mark.parametrize('precision', ['double', 'half'])
+def test_restart_after_missed_certificate(precision):
+    """Reading 7: a solve whose FP64 full-lattice certificate misses tol resumes from
+    its x.  The testing knob makes the Schur stopping norm 100 times too loose, so
+    the first certificate misses 1e-10; with restarts the solve still returns a
+    certified x equal to the oracle's solution, without them it reports
+    NOT_CONVERGED."""
+    L = Lat(*CASES[0])
+    try:
+        b = np.zeros(L.shape, dtype=np.complex128)
+        b[0, 0, 0, 0, 0, 0, 0] = 1.0
+        with pytest.raises(M.MdwfError) as e:
+            M.mdwf_solve(L.ctx, 0, b, 1e-10, M.mdwf_default_opts(precision=precision, stop_scale_test=100.0,
+                                                                 max_restarts=0))
+        assert e.value.code == M.MDWF_ERR_NOT_CONVERGED
+        x, st = M.mdwf_solve(L.ctx, 0, b, 1e-10, M.mdwf_default_opts(precision=precision, stop_scale_test=100.0))
+        assert st['restarts'] >= 1
+        _check_solution(L, b, x, st)
+        ref, _ = O.solve_schur(L.U, b, *L.act, tol=1e-13)
+        assert _rel(x, ref) < 1e-8
     finally:
         L.close()
 
