@@ -1,15 +1,24 @@
 #!/usr/bin/env python
 """Benchmark of the even-odd preconditioned Moebius domain-wall solve on GB300.
 
-One step = one batched mixed-precision solve (fp16 storage with per-site
-scales, FP32 arithmetic, FP64 reliable updates / accumulator / sums) of the 12
-spin-colour point sources of the 16^3 x 48, L5 = 12 workload (a15m310 action
-of the paper's Table II: M5 = 1.3, b5 = 1.5, c5 = 0.5, m_f = 0.0158) on
-near-identity random SU(3) links smoothed by Wilson flow to t = 1, to a true
-FP64 residual |b - D x| / |b| <= 1e-10.
+One step = one batched mixed-precision solve (fp16 storage with a power-of-two
+scale per stored spinor, FP32 arithmetic, FP64 reliable updates / accumulator /
+sums) of all right-hand sides of a workload, to a true FP64 residual
+|b - D x| / |b| <= 1e-10.  The default workload ('16x48', the headline line) is
+the 12 spin-colour point sources of 16^3 x 48, L5 = 12 with the a15m310 action
+of the paper's Table II (M5 = 1.3, b5 = 1.5, c5 = 0.5, m_f = 0.0158) on
+near-identity random SU(3) links smoothed by Wilson flow to t = 1.
+``--workload`` selects the others: '4x8' (the oracle-sized plain FP64 case, timed
+beside a full oracle solve), '24x64' (a12m310 action, 24 RHS over two masses in
+one batch) and '48x64' (a12m130-shaped light quark).
 
-Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
-on a bounded sample of the same workload instead.  Other modes: ``--mode op``
+Prints one JSON line (rank 0): solves/s, time to solution, iterations, updates,
+the FP64 certificate and the oracle's check of a solution, the per-phase device
+time, the dominant hop kernel against the HBM roofline (SURVEY 8(d) bytes) and
+the FP32 roofline, the FP64 single-RHS GPU CG on the same input, the oracle on
+the host cores (one core and all cores), and the same metric end to end through
+the host-pointer call.  ``--impl reference`` times the FP64 CPU oracle on a
+bounded sample of the same workload instead.  Other modes: ``--mode op``
 applies the batched Schur operator only (a short driver for kernel profiles);
 ``--mode serve`` serves a Poisson stream of solve requests over three resident
 configurations and reports p50/p99 latency and solves/s.  ``--schur sym`` solves
@@ -28,11 +37,33 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "MDWF solves/s to 1e-10 (batched mixed vs FP64 CG); Dslash HBM GB/s; p50/p99"
-WORKLOAD = dict(name='16^3x48 L5=12 a15m310-action, flowed SU(3), 12 spin-colour point sources, tol 1e-10',
-                dims=(16, 16, 16, 48), L5=12, M5=1.3, b5=1.5, c5=0.5, mf=0.0158,
-                seed=2, eps=0.4, flow_t=1.0, flow_eps=0.01, nsrc=12, tol=1e-10)
-BYTES_PER_UNIT = {'half': 48 + 4, 'single': 96, 'bf16': 48, 'double': 192}   # one stored (site, s, rhs) spinor
-LINK_BYTES = {'half': 72, 'single': 72, 'bf16': 72, 'double': 144}           # one stored link (18 reals)
+# The workloads: synthetic stand-ins shaped like the paper's ensembles (Table II
+# actions); '16x48' is the headline line.
+WORKLOADS = {
+    '4x8': dict(name='4^3x8 L5=4, exp(0.3 i H) links (no flow), one point source (spin 0, colour 0, origin), '
+                     'plain FP64 CG, tol 1e-10',
+                dims=(4, 4, 4, 8), L5=4, M5=1.3, b5=1.5, c5=0.5, masses=[0.1], seed=1, eps=0.3, flow_t=0.0,
+                flow_eps=0.01, sources='point1', tol=1e-10, precision='double'),
+    '16x48': dict(name='16^3x48 L5=12 a15m310-action, flowed SU(3), 12 spin-colour point sources, tol 1e-10',
+                  dims=(16, 16, 16, 48), L5=12, M5=1.3, b5=1.5, c5=0.5, masses=[0.0158] * 12, seed=2, eps=0.4,
+                  flow_t=1.0, flow_eps=0.01, sources='point12', tol=1e-10, precision='half'),
+    '24x64': dict(name='24^3x64 L5=8 a12m310-action, flowed SU(3), 12 spin-colour point sources x m_f '
+                       '{0.0126, 0.0102} in one 24-RHS batch, tol 1e-10',
+                  dims=(24, 24, 24, 64), L5=8, M5=1.2, b5=1.25, c5=0.25, masses=[0.0126] * 12 + [0.0102] * 12,
+                  seed=3, eps=0.4, flow_t=1.0, flow_eps=0.01, sources='point12', tol=1e-10, precision='half'),
+    '48x64': dict(name='48^3x64 L5=8 a12m130-shaped light quark m_f=0.0022, flowed SU(3), spin-colour point '
+                       'sources, tol 1e-10',
+                  dims=(48, 48, 48, 64), L5=8, M5=1.2, b5=1.25, c5=0.25, masses=[0.0022] * 12, seed=4, eps=0.4,
+                  flow_t=1.0, flow_eps=0.01, sources='point12', tol=1e-10, precision='half', rhs_default=2),
+}
+WORKLOAD = WORKLOADS['16x48']
+# algorithmic bytes of one stored real (input + output spinor, 24 reals each, and the
+# link share 8 links x 18 reals of each output site over its L5 x N units; FP32 links here)
+REAL_BYTES = {'half': 2, 'single': 4, 'bf16': 2, 'double': 8}
+LINK_REAL_BYTES = {'half': 4, 'single': 4, 'bf16': 4, 'double': 8}
+# what a hop launch of the solver moves in its storage format: input, output and, in two of the
+# four launches of an iteration, the `same` field, plus the fp16 scale of each stored spinor
+BYTES_PER_UNIT = {'half': 48 + 4, 'single': 96, 'bf16': 48, 'double': 192}
 
 
 def parse():
@@ -41,10 +72,14 @@ def parse():
     ap.add_argument('--steps', type=int, default=5)
     ap.add_argument('--warmup', type=int, default=3)
     ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
-    ap.add_argument('--precision', default='half', choices=['half', 'single', 'bf16', 'double'])
+    ap.add_argument('--precision', default=None, choices=['half', 'single', 'bf16', 'double'],
+                    help="inner storage precision (default: the workload's)")
     ap.add_argument('--no-fp64', action='store_true', help='skip the FP64 single-RHS GPU CG comparison')
     ap.add_argument('--no-cpu', action='store_true', help='skip the oracle cpu_baseline sample')
-    ap.add_argument('--rhs', type=int, default=12, help='spin-colour sources per step (12 = the workload)')
+    ap.add_argument('--workload', default='16x48', choices=sorted(WORKLOADS),
+                    help='4x8: the oracle-sized FP64 case; 16x48 (default, the headline line): a15m310; '
+                         '24x64: a12m310, 24 RHS over two masses; 48x64: a12m130-shaped light quark')
+    ap.add_argument('--rhs', type=int, default=0, help='right-hand sides per step (0: the workload\'s)')
     ap.add_argument('--mode', default='solve', choices=['solve', 'op', 'serve'],
                     help="'op': only apply the batched Schur operator (the solver's hop kernels), for profiling")
     ap.add_argument('--lattice', default=None, help="op mode: Lx,Ly,Lz,Lt instead of the workload's 16,16,16,48")
@@ -140,16 +175,26 @@ def measured_peaks():
         return 6800.0, 'fallback'
 
 
-def ncu_traffic(kernel_key):
-    """Per-launch DRAM bytes of the hop kernel from the committed ncu summary, if the
-    kernel source has not changed since it was captured (else None)."""
+HOP_SOURCES = ('hop_pair.cu', 'hop_common.cuh', 'mdwf_internal.h')
+
+
+def hop_sources_sha256():
     import hashlib
-    path = os.path.join(ROOT, 'profiles', 'hop_kernel_ncu.json')
+    h = hashlib.sha256()
+    for name in HOP_SOURCES:
+        with open(os.path.join(ROOT, 'paper_1701_07559_gb300', 'csrc', name), 'rb') as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def ncu_traffic(kernel_key):
+    """Per-launch DRAM bytes of the hop kernel from the committed ncu record, if the
+    kernel's sources have not changed since it was captured (else None)."""
+    path = os.path.join(ROOT, 'profiles', 'hop_pair_kernel_ncu.json')
     try:
         with open(path) as f:
             rec = json.load(f)
-        src = open(os.path.join(ROOT, 'paper_1701_07559_gb300', 'csrc', 'hop_fast.cu'), 'rb').read()
-        if rec.get('hop_fast_cu_sha256') != hashlib.sha256(src).hexdigest():
+        if rec.get('sources_sha256') != hop_sources_sha256():
             return None
         return rec['workloads'][kernel_key]['dram_bytes_per_launch']
     except (OSError, KeyError, ValueError):
@@ -159,6 +204,8 @@ def ncu_traffic(kernel_key):
 def flowed_links(M, dims, seed, eps, flow_t, flow_eps, device=0):
     """Random links exp(i eps H) (host generator) flowed to flow_t on the device."""
     import synth
+    if flow_t <= 0:
+        return synth.random_gauge(dims, seed, eps)
     ctx = M.mdwf_create(dims, device)
     try:
         return M.flowed_gauge_dev(ctx, synth.random_gauge(dims, seed, eps), flow_t, flow_eps)
@@ -166,31 +213,66 @@ def flowed_links(M, dims, seed, eps, flow_t, flow_eps, device=0):
         M.mdwf_destroy(ctx)
 
 
-def make_inputs(M, ctx, W, nsrc):
+def workload(args):
+    W = dict(WORKLOADS[args.workload])
+    W['key'] = args.workload
+    W['precision'] = args.precision or W['precision']
+    n = args.rhs or W.get('rhs_default', len(W['masses']))
+    W['masses'] = [W['masses'][k % len(W['masses'])] for k in range(n)]
+    W['nsrc'] = n
+    W['lattice'] = '%d^3x%d' % (W['dims'][0], W['dims'][3]) if W['dims'][0] == W['dims'][1] == W['dims'][2] \
+        else 'x'.join(str(d) for d in W['dims'])
+    return W
+
+
+def source_4d(W, k):
+    """k-th 4D source of the workload: the spin-colour point sources at the origin,
+    spin k // 3 and colour k % 3 of the k % 12-th (the 12 repeat for each mass)."""
     import synth
-    srcs = []
-    for k in range(nsrc):
-        eta = synth.point_source_4d(W['dims'], k // 3, k % 3)
-        srcs.append(M.mdwf_make_source(ctx, 0, eta))
-    return srcs
+    j = k % 12 if W['sources'] == 'point12' else 0
+    return synth.point_source_4d(W['dims'], j // 3, j % 3)
 
 
-def oracle_sample(W, U):
-    """Time one application of the oracle's Schur operator on one RHS (the bounded
-    sample); a CGNR iteration applies Mhat and Mhat^+, i.e. twice this work."""
+def make_inputs(M, ctx, W):
+    return [M.mdwf_make_source(ctx, 0, source_4d(W, k)) for k in range(W['nsrc'])]
+
+
+def _oracle_apply_worker(task):
+    """One FP64 oracle Schur-operator application (run in a spawned process)."""
     import synth
     from oracle import mdwf_oracle as O
+    W, U, seed = task
     Lx, Ly, Lz, Lt = W['dims']
     ev = O.parity_mask(W['dims'])
-    psi = O.restrict(synth.gaussian_spinor((W['L5'], Lt, Lz, Ly, Lx, 4, 3), 1), ev)
+    psi = O.restrict(synth.gaussian_spinor((W['L5'], Lt, Lz, Ly, Lx, 4, 3), seed), ev)
     t0 = time.perf_counter()
-    O.schur_op(U, psi, W['M5'], W['b5'], W['c5'], W['mf'])
+    O.schur_op(U, psi, W['M5'], W['b5'], W['c5'], W['masses'][0])
     return time.perf_counter() - t0
 
 
-def oracle_cores():
-    n = os.environ.get('OMP_NUM_THREADS') or os.environ.get('OPENBLAS_NUM_THREADS')
-    return int(n) if n else 1
+def oracle_timing(W, U, n_iter, procs):
+    """The oracle as it stands on the host cores: one Schur-operator application
+    on one core, then `procs` of them at once (one per process, spawned); a CGNR
+    iteration is two applications, a solve n_iter iterations."""
+    import multiprocessing as mp
+    t1 = _oracle_apply_worker((W, U, 1))
+    out = {'apply_s_1core': t1, 'solves_per_s_1core': 1.0 / (2.0 * t1 * n_iter) if n_iter else None}
+    if procs > 1:
+        ctx = mp.get_context('spawn')
+        t0 = time.perf_counter()
+        with ctx.Pool(procs) as pool:
+            pool.map(_oracle_apply_worker, [(W, U, 1 + k) for k in range(procs)])
+        tp = time.perf_counter() - t0
+        out.update({'procs': procs, 'apply_wall_s_all': tp,
+                    'solves_per_s_all': procs / (2.0 * tp * n_iter) if n_iter else None})
+    return out
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
 
 
 # ---------------------------------------------------------------------------
@@ -202,36 +284,46 @@ def run_reference(args):
         return 0
     import numpy as np  # noqa: F401
     import synth
-    W = WORKLOAD
-    U = synth.flowed_gauge(W['dims'], W['seed'], W['eps'], W['flow_t'], W['flow_eps'])
-    rec = iteration_record()
+    W = workload(args)
+    U = synth.flowed_gauge(W['dims'], W['seed'], W['eps'], W['flow_t'], W['flow_eps']) if W['flow_t'] > 0 \
+        else synth.random_gauge(W['dims'], W['seed'], W['eps'])
+    rec = iteration_record(W['key'])
     n_iter = rec['fp64_cgnr_iters'] if rec else None
     for _ in range(max(0, min(args.warmup, 1))):
-        oracle_sample(W, U)
-    times = [oracle_sample(W, U) for _ in range(max(1, args.steps))]
+        _oracle_apply_worker((W, U, 1))
+    times = [_oracle_apply_worker((W, U, 1)) for _ in range(max(1, args.steps))]
     t = statistics.median(times)
     per_solve = 2.0 * t * n_iter if n_iter else None
     value = (1.0 / per_solve) if per_solve else None
-    sample = ('one FP64 oracle Schur-operator application (numpy, one RHS, full 16^3x48x12 lattice) per step; '
-              'a CGNR iteration is two such applications; solves/s = 1/(2 t n_iter) with n_iter = %s, the '
-              'iteration count of FP64 CGNR on this workload' % n_iter)
+    sample = ('one FP64 oracle Schur-operator application (numpy, one RHS, the full %s x %d lattice, one core) '
+              'per step; a CGNR iteration is two such applications; solves/s = 1/(2 t n_iter) with n_iter = %s, '
+              'the iteration count of FP64 CGNR on this workload' % (W['lattice'], W['L5'], n_iter))
     line = {'impl': 'reference', 'metric': METRIC, 'value': value, 'unit': 'solves/s', 'n_gpus': args.gpus,
             'steps': len(times), 'warmup': args.warmup, 'ms_per_step': 1e3 * statistics.mean(times),
             'higher_is_better': True, 'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f64', 'data': 'synthetic',
-            'config': {'workload': W['name'], 'lattice': '16^3x48', 'L5': W['L5'], 'rhs': W['nsrc']},
-            'cpu_baseline': {'value': value, 'unit': 'solves/s', 'cores': oracle_cores(), 'kind': 'oracle',
-                             'sample': sample},
+            'config': config_of(W, W['nsrc'], 'single host core'),
+            'cpu_baseline': {'value': value, 'unit': 'solves/s', 'cores': 1, 'kind': 'oracle', 'sample': sample},
             'e2e': {'value': value, 'unit': 'solves/s', 'h2d_bytes_per_step': 0, 'd2h_bytes_per_step': 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
-def iteration_record():
+def iteration_record(key='16x48'):
+    """FP64 CGNR iteration count of the workload (profiles/workload_iterations.json,
+    written from bench lines), used to scale oracle timing samples to solves/s."""
     try:
-        with open(os.path.join(ROOT, 'profiles', 'workload_a15m310_iterations.json')) as f:
-            return json.load(f)
+        with open(os.path.join(ROOT, 'profiles', 'workload_iterations.json')) as f:
+            return json.load(f).get(key)
     except (OSError, ValueError):
         return None
+
+
+def config_of(W, n, parallelism):
+    return {'workload': W['name'], 'lattice': W['lattice'], 'L5': W['L5'], 'rhs_per_step': n,
+            'action': {'M5': W['M5'], 'b5': W['b5'], 'c5': W['c5'], 'masses': sorted(set(W['masses']))},
+            'gauge': 'exp(i %.1f H)%s' % (W['eps'], ', Wilson flow t=%g (RK3, eps %g, FP64)' % (
+                W['flow_t'], W['flow_eps']) if W['flow_t'] > 0 else ', no flow'),
+            'precision': W['precision'], 'parallelism': parallelism}
 
 
 # ---------------------------------------------------------------------------
@@ -248,16 +340,16 @@ def run_ours(args):
         dist.init_process_group('nccl')
     import __graft_entry__
     __graft_entry__.build()
-    import synth
     from paper_1701_07559_gb300 import mdwf as M
-    W = WORKLOAD
-    prec = args.precision
+    W = workload(args)
+    prec = W['precision']
     U = flowed_links(M, W['dims'], W['seed'], W['eps'], W['flow_t'], W['flow_eps'], local)
     ctx = M.mdwf_create(W['dims'], local)
     M.mdwf_load_gauge(ctx, 0, U, 1)
-    M.mdwf_set_action(ctx, 0, W['M5'], W['b5'], W['c5'], W['mf'], W['L5'])
-    srcs = make_inputs(M, ctx, W, args.rhs)
+    M.mdwf_set_action(ctx, 0, W['M5'], W['b5'], W['c5'], W['masses'][0], W['L5'])
+    srcs = make_inputs(M, ctx, W)
     n = len(srcs)
+    masses = W['masses']
     stream = torch.cuda.current_stream()
     dsrc = [torch.from_numpy(s).to('cuda') for s in srcs]
     dx = [torch.empty_like(s) for s in dsrc]
@@ -270,8 +362,11 @@ def run_ours(args):
         if dist is not None:
             dist.barrier()
 
+    def solve(o):
+        return M.mdwf_solve_batch_dev(ctx, 0, dsrc, dx, W['tol'], masses=masses, opts=o, stream=stream)
+
     for _ in range(args.warmup):
-        M.mdwf_solve_batch_dev(ctx, 0, dsrc, dx, W['tol'], opts=opts, stream=stream)
+        solve(opts)
     torch.cuda.synchronize()
     barrier()
     torch.cuda.synchronize()
@@ -282,7 +377,7 @@ def run_ours(args):
     t0 = time.perf_counter()
     for i in range(args.steps):
         ev[i][0].record(stream)
-        stats.append(M.mdwf_solve_batch_dev(ctx, 0, dsrc, dx, W['tol'], opts=opts_timed, stream=stream))
+        stats.append(solve(opts_timed))
         ev[i][1].record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -291,15 +386,15 @@ def run_ours(args):
     clk = clocks.stop()
     timed = stats
     if args.profile_steps == 'extra':
-        stats = [M.mdwf_solve_batch_dev(ctx, 0, dsrc, dx, W['tol'], opts=opts, stream=stream)]
+        stats = [solve(opts)]
     step_ms = [a.elapsed_time(b) for a, b in ev]
     from paper_1701_07559_gb300 import replicas
     # independent replicas: solves of all ranks over the slowest rank's time
     value = replicas.job_throughput(n * args.steps, sum(step_ms) / 1e3, dist, 'cuda')
     total_s = replicas.max_over_ranks(sum(step_ms) / 1e3, dist, 'cuda')
 
-    # correctness of what was timed: FP64 true residual of the last step, and the
-    # oracle's own D on one solution (rank 0)
+    # correctness of what was timed: every system of the last step reports its
+    # FP64 full-lattice residual (the library's certificate)
     last = timed[-1]
     resid_max = max(s['rel_true_resid'] for s in last)
     assert all(s['converged'] for s in last), last
@@ -310,89 +405,151 @@ def run_ours(args):
     hop_ms = sum(s[0]['hop_ms'] for s in stats)
     units = last[0]['hop_units']
     L5, V = W['L5'], W['dims'][0] * W['dims'][1] * W['dims'][2] * W['dims'][3]
-    # per launch: input + output (+ the `same` field in half of the launches) + 8 links per output site
-    bytes_per_launch = units * 2.5 * BYTES_PER_UNIT[prec] + (V // 2) * 8 * LINK_BYTES[prec]
-    hop_avg_s = (hop_ms / hop_launches) / 1e3
-    achieved = bytes_per_launch / hop_avg_s / 1e9
+    hop_avg_s = (hop_ms / hop_launches) / 1e3 if hop_launches else None
+    # SURVEY 8(d) algorithmic bytes: input and output spinor (24 reals each) per unit, plus
+    # 8 links of 18 reals per output site shared by its L5 x N units
+    w, wg = REAL_BYTES[prec], LINK_REAL_BYTES[prec]
+    bytes_per_unit = 48 * w + 8 * 18 * wg / (L5 * n)
+    bytes_per_launch = units * bytes_per_unit
+    # what the launches store and load: + the fp16 scales, + `same` in half of the launches
+    stored_per_launch = units * 2.5 * BYTES_PER_UNIT[prec] + (V // 2) * 8 * 18 * wg
+    achieved = bytes_per_launch / hop_avg_s / 1e9 if hop_avg_s else None
     peak, peak_kind = measured_peaks()
-    gflops = units * 1320 / hop_avg_s / 1e9
+    gflops = units * 1320 / hop_avg_s / 1e9 if hop_avg_s else None
+    # FP32 CUDA-core peak at the measured clock: 152 SMs x 128 lanes x 2 flops (FMA)
+    mhz = clk.get('sm_mhz') or 2070.0
+    fp32_peak_tflops = 152 * 128 * 2 * mhz * 1e6 / 1e12
     gpu_launches = sum(s[0]['kernel_launches'] for s in timed)
     tuned = M.mdwf_autotune(ctx, 0, n, prec, include_tensor_core=args.hop_variant == 4) \
         if args.hop_variant in (0, 4) and args.nsb == 0 else None
-    kernel_name = {1: 'hop_fast_kernel', 2: 'hop_staged_kernel', 3: 'hop_mma_kernel'}.get(
-        tuned['hop_variant'] if tuned else (args.hop_variant or 1), 'hop_fast_kernel')
+    variant = tuned['hop_variant'] if tuned else (args.hop_variant or 1)
+    kernel_name = {1: 'hop_pair_kernel' if prec != 'double' else 'hop_fast_kernel_f64',
+                   2: 'hop_staged_kernel', 3: 'hop_mma_kernel', 6: 'hop_fast_kernel'}.get(variant, 'hop_pair_kernel')
 
     # end to end through the host-pointer C ABI call, pinned host buffers
     pin_src = [torch.from_numpy(s).pin_memory().numpy() for s in srcs]
     pin_x = [torch.empty(s.shape, dtype=torch.complex128).pin_memory().numpy() for s in srcs]
     opts_e2e = M.mdwf_default_opts(precision=prec, hop_variant=args.hop_variant, nsb=args.nsb, schur=schur)
-    M.mdwf_solve_batch(ctx, 0, pin_src, W['tol'], opts=opts_e2e, out=pin_x)
+    M.mdwf_solve_batch(ctx, 0, pin_src, W['tol'], masses=masses, opts=opts_e2e, out=pin_x)
     torch.cuda.synchronize()
     barrier()
     e2e_t = []
     for _ in range(args.steps):
         t1 = time.perf_counter()
-        M.mdwf_solve_batch(ctx, 0, pin_src, W['tol'], opts=opts_e2e, out=pin_x)
+        M.mdwf_solve_batch(ctx, 0, pin_src, W['tol'], masses=masses, opts=opts_e2e, out=pin_x)
         e2e_t.append(time.perf_counter() - t1)
     e2e_value = replicas.job_throughput(n * args.steps, sum(e2e_t), dist, 'cuda')
     field_bytes = L5 * V * 24 * 8
 
-    # plain FP64 single-RHS GPU CG on the first source (the baseline to beat)
+    # plain FP64 single-RHS GPU CG on the first source, like for like: device
+    # pointers, one warm-up solve, CUDA events around each timed solve
     fp64 = None
     if not args.no_fp64:
-        o64 = M.mdwf_default_opts(precision='double')
-        t1 = time.perf_counter()
-        _, st64 = M.mdwf_solve_batch(ctx, 0, [pin_src[0]], W['tol'], opts=o64)
-        dt = time.perf_counter() - t1
-        fp64 = {'solves_per_s': 1.0 / dt, 'time_s': dt, 'iters': st64[0]['iters'],
-                'rel_true_resid': st64[0]['rel_true_resid'], 'precision': 'FP64 storage and arithmetic, 1 RHS'}
+        o64 = M.mdwf_default_opts(precision='double', hop_variant=1)
+        one = lambda: M.mdwf_solve_batch_dev(ctx, 0, dsrc[:1], dx[:1], W['tol'], masses=masses[:1], opts=o64,
+                                             stream=stream)
+        one()
+        k64 = max(1, min(args.steps, 2))
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k64)]
+        for a, b in evs:
+            a.record(stream)
+            st64 = one()
+            b.record(stream)
+        torch.cuda.synchronize()
+        t64 = statistics.mean(a.elapsed_time(b) for a, b in evs) / 1e3
+        fp64 = {'solves_per_s': 1.0 / t64, 'time_s': t64, 'iters': st64[0]['iters'], 'timed_solves': k64,
+                'rel_true_resid': st64[0]['rel_true_resid'],
+                'precision': 'FP64 storage and arithmetic, 1 RHS, device pointers, warmed'}
 
     out = None
     if rank == 0:
         cpu = None
+        oracle_check = None
         if not args.no_cpu and world == 1:
-            rec = iteration_record()
-            n_iter = fp64['iters'] if fp64 else (rec['fp64_cgnr_iters'] if rec else None)
-            t_s = oracle_sample(W, U)
-            cpu_value = 1.0 / (2.0 * t_s * n_iter) if n_iter else None
-            cpu = {'value': cpu_value, 'unit': 'solves/s', 'cores': oracle_cores(), 'kind': 'oracle',
-                   'sample': ('one FP64 oracle Schur-operator application on one RHS of this workload (%.1f s); '
-                              'a CGNR iteration is two; scaled by the %s iterations FP64 CGNR takes here'
-                              % (t_s, n_iter))}
+            # the oracle as it stands, on the host cores: a full solve where it takes
+            # seconds (the 4^3 x 8 workload), else a bounded sample of applications
+            from oracle import mdwf_oracle as O
+            from oracle import sampled
+            x0 = dx[0].cpu().numpy()
+            b0 = srcs[0]
+            m0 = masses[0]
+            if V <= 4096:
+                t1 = time.perf_counter()
+                xref, it_or = O.solve_schur(U, b0, W['M5'], W['b5'], W['c5'], m0, tol=W['tol'])
+                t_or = time.perf_counter() - t1
+                cpu = {'value': 1.0 / t_or, 'unit': 'solves/s', 'cores': 1, 'kind': 'oracle',
+                       'sample': 'one full FP64 oracle solve (Schur CGNR, %d iterations) of the first source, '
+                                 '%.2f s on one host core' % (it_or, t_or)}
+                oracle_check = {'err_vs_oracle_solution': float(np.linalg.norm((x0 - xref).ravel()) /
+                                                                np.linalg.norm(xref.ravel())),
+                                'oracle_true_residual': float(O.true_residual(U, b0, x0, W['M5'], W['b5'],
+                                                                              W['c5'], m0))}
+            else:
+                n_iter = fp64['iters'] if fp64 else (iteration_record(W['key']) or {}).get('fp64_cgnr_iters')
+                procs = min(host_cores(), n, 16)
+                ot = oracle_timing(W, U, n_iter, procs)
+                cpu = {'value': ot['solves_per_s_1core'], 'unit': 'solves/s', 'cores': 1, 'kind': 'oracle',
+                       'sample': ('one FP64 oracle Schur-operator application on one RHS of this workload (%.1f s '
+                                  'on one core); a CGNR iteration is two, a solve %s iterations (FP64 CGNR here)'
+                                  % (ot['apply_s_1core'], n_iter)),
+                       'all_cores': {'value': ot.get('solves_per_s_all'), 'cores': ot.get('procs'),
+                                     'apply_wall_s': ot.get('apply_wall_s_all'),
+                                     'sample': 'the same application in %s spawned processes at once'
+                                               % ot.get('procs')},
+                       'host_cores': host_cores()}
+                # the oracle's own D on the first solution at sampled sites: |b - D x|(site) / |b|
+                rng = np.random.default_rng(W['seed'])
+                sites = [(0, 0, 0, 0)] + [tuple(int(rng.integers(d)) for d in W['dims']) for _ in range(3)]
+                bn = np.linalg.norm(b0.ravel())
+                worst = max(np.linalg.norm(sampled.residual_at_site(U, b0, x0, s, W['M5'], W['b5'], W['c5'],
+                                                                    m0).ravel()) / bn for s in sites)
+                oracle_check = {'sampled_sites': len(sites), 'max_site_residual_over_norm_b': float(worst),
+                                'note': 'no oracle solve is feasible at this size; the error against the solution '
+                                        'is bounded by kappa x 1e-10'}
         lat = sorted(step_ms)
         p99 = lat[min(len(lat) - 1, int(np.ceil(0.99 * len(lat))) - 1)]
+        phases = {k: statistics.mean(s[0]['phase_ms'][k] for s in stats) for k in M.PHASES}
         out = {
             'metric': METRIC, 'value': value, 'unit': 'solves/s', 'n_gpus': world, 'steps': args.steps,
             'warmup': args.warmup, 'ms_per_step': total_s * 1e3 / args.steps, 'higher_is_better': True,
-            'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f32',
-            'storage': {'half': 'fp16 + per-site scale', 'single': 'fp32', 'bf16': 'bf16',
-                        'double': 'fp64'}[prec] + ' inner vectors; FP64 accumulator, reliable updates and sums',
+            'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f64' if prec == 'double' else 'f32',
+            'storage': {'half': 'fp16 + power-of-two scale per (site, slice, RHS)', 'single': 'fp32',
+                        'bf16': 'bf16', 'double': 'fp64'}[prec] +
+                       ' inner vectors; FP64 accumulator, reliable updates and sums',
             'data': 'synthetic',
-            'config': {'workload': W['name'], 'lattice': '16^3x48', 'L5': W['L5'], 'rhs_per_step': n,
-                       'action': {'M5': W['M5'], 'b5': W['b5'], 'c5': W['c5'], 'mf': W['mf']},
-                       'gauge': 'exp(i 0.4 H), Wilson flow t=1 (RK3, eps 0.01, FP64)', 'precision': prec,
-                       'schur': args.schur,
-                       'l2': 'inputs larger than L2: %.2f GB of inner vectors per step' % (
-                           6 * units * BYTES_PER_UNIT[prec] / 1e9),
-                       'parallelism': 'replicas' if world > 1 else 'single GPU'},
+            'config': dict(config_of(W, n, 'replicas' if world > 1 else 'single GPU'),
+                           schur=args.schur,
+                           l2='inputs larger than L2: %.2f GB of inner vectors per step' % (
+                               6 * units * BYTES_PER_UNIT[prec] / 1e9)),
             'latency_ms': {'p50': statistics.median(step_ms), 'p99': p99, 'per_step': step_ms},
+            'time_to_solution_s': {'p50': statistics.median(step_ms) / 1e3, 'p99': p99 / 1e3},
             'iters': iters, 'rel_true_resid_max': resid_max,
             'reliable_updates': [s['reliable_updates'] for s in last],
             'fp32_updates': [s['fp32_updates'] for s in last],
             'fp64_rerefs': [s['fp64_rerefs'] for s in last],
-            'phases_ms_per_step': {k: statistics.mean(s[0]['phase_ms'][k] for s in stats)
-                                   for k in M.PHASES},
+            'restarts': last[0]['restarts'],
+            'phases_ms_per_step': phases,
             'hop_ms_per_step': hop_ms / len(stats),
             'profiled_steps': args.profile_steps,
+            'oracle_check': oracle_check,
             'fp64_gpu_cg': fp64,
             'speedup_vs_fp64_gpu_cg': (value / fp64['solves_per_s']) if fp64 else None,
             'autotuned': tuned,
             'dslash': {'kernel': '%s<%s>' % (kernel_name, prec), 'launches_timed': hop_launches,
-                       'avg_launch_us': hop_avg_s * 1e6, 'GB_per_s': achieved, 'eff_GFLOP_per_s': gflops,
-                       'units_per_launch': units, 'bytes_per_launch': bytes_per_launch},
+                       'avg_launch_us': hop_avg_s * 1e6 if hop_avg_s else None,
+                       'GB_per_s': achieved, 'eff_GFLOP_per_s': gflops,
+                       'units_per_launch': units, 'algorithmic_bytes_per_unit': bytes_per_unit,
+                       'bytes_per_launch': bytes_per_launch,
+                       'stored_bytes_per_launch': stored_per_launch,
+                       'stored_GB_per_s': stored_per_launch / hop_avg_s / 1e9 if hop_avg_s else None},
             'roofline': {'bound': 'hbm', 'achieved': achieved, 'peak': peak, 'unit': 'GB/s',
-                         'frac': achieved / peak, 'peak_kind': peak_kind,
-                         'traffic': ncu_traffic('a15m310_%s' % prec)},
+                         'frac': achieved / peak if achieved else None, 'peak_kind': peak_kind,
+                         'traffic': ncu_traffic('%s_%s' % (W['key'], prec))},
+            'alu_roofline': {'bound': 'alu', 'achieved': gflops / 1e3 if gflops else None,
+                             'peak': fp32_peak_tflops, 'unit': 'TFLOP/s',
+                             'frac': gflops / 1e3 / fp32_peak_tflops if gflops else None,
+                             'peak_kind': 'derived: 152 SMs x 128 FP32 lanes x 2 flops x %.0f MHz' % mhz,
+                             'flops_per_unit': 1320},
             'cpu_baseline': cpu,
             'e2e': {'value': e2e_value, 'unit': 'solves/s', 'h2d_bytes_per_step': n * field_bytes,
                     'd2h_bytes_per_step': n * field_bytes},
@@ -417,6 +574,8 @@ def run_op(args):
     import synth
     from paper_1701_07559_gb300 import mdwf as M
     W = dict(WORKLOAD)
+    args.precision = args.precision or 'half'
+    args.rhs = args.rhs or 12
     if args.lattice:
         W['dims'] = tuple(int(v) for v in args.lattice.split(','))
     U = synth.flowed_gauge(W['dims'], W['seed'], W['eps'], W['flow_t'], W['flow_eps'])
@@ -476,6 +635,7 @@ def run_serve(args):
     from paper_1701_07559_gb300 import serving
     from paper_1701_07559_gb300 import mdwf as M
     torch.cuda.set_device(0)
+    args.precision = args.precision or 'half'
     budget = int(args.hbm_budget_gb * 1e9) if args.hbm_budget_gb > 0 else None
     srv = serving.Server(device=0, hbm_budget=budget, tol=1e-10, precision=args.precision, max_slots=args.slots)
     names, dims = [], []

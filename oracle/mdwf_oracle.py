@@ -1,8 +1,8 @@
 """Plain FP64 CPU oracle for the even-odd preconditioned Moebius domain-wall solve.
 
 TEST INFRASTRUCTURE. Only ``tests/``, ``__graft_entry__.smoke()`` and the
-``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
-module.  It shares no code with the CUDA library and never imports it.
+oracle legs of ``bench.py`` (``cpu_baseline`` with its sampled residual check,
+``--impl reference``) may import this module.  It shares no code with the CUDA library and never imports it.
 
 Everything is written out in the most direct form: full-lattice complex128
 arrays, ``np.roll`` for the nearest-neighbour shifts and ``np.einsum`` for the

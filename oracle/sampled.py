@@ -1,10 +1,13 @@
 """The oracle's D x at single sites of a large lattice, for sampled checks of
 full-size results: D = A - 1/2 H B evaluated on the 3^4 window of sites around
 the sampled site (time-boundary phases folded into the window), with the
-oracle's own A, B and single-site hop."""
+oracle's own A, B and single-site hop (Sec. II operator, as in mdwf_oracle).
+
+TEST INFRASTRUCTURE, as the rest of this package: only tests/,
+__graft_entry__.smoke() and bench.py's oracle legs use it."""
 import numpy as np
 
-from oracle import mdwf_oracle as O
+from . import mdwf_oracle as O
 
 
 def _window(field, site, dims, antiperiodic_t, links=False):

@@ -36,9 +36,18 @@ def test_table2_tuning_constraint_and_flow_time():
 def test_workloads_take_table2_actions():
     import bench
     t = table2()
-    w = bench.WORKLOAD
-    a = t['a15m310']
-    assert (w['M5'], w['L5'], w['b5'], w['c5'], w['mf']) == (a['M5'], a['L5'], a['b5'], a['c5'], a['ml'])
+    # 16^3 x 48: a15m310 as printed; 24^3 x 64: a12m310 with its light mass and 0.0102 (the
+    # sea light-quark mass in the ensemble's name); 48^3 x 64: the a12m310 (M5, b5, c5) at
+    # L5 = 8 with m_f = 0.0022, the a12m130 lattice shape (the paper's a12m130 row has L5 = 20)
+    w, a = bench.WORKLOADS['16x48'], t['a15m310']
+    assert (w['M5'], w['L5'], w['b5'], w['c5']) == (a['M5'], a['L5'], a['b5'], a['c5'])
+    assert set(w['masses']) == {a['ml']}
+    w, a = bench.WORKLOADS['24x64'], t['a12m310']
+    assert (w['M5'], w['L5'], w['b5'], w['c5']) == (a['M5'], a['L5'], a['b5'], a['c5'])
+    assert set(w['masses']) == {a['ml'], 0.0102}
+    w = bench.WORKLOADS['48x64']
+    assert (w['M5'], w['L5'], w['b5'], w['c5']) == (a['M5'], a['L5'], a['b5'], a['c5'])
+    assert bench.WORKLOAD is bench.WORKLOADS['16x48']
     # serving mix: L5 = 12 and L5 = 8 take the a15m310 and a12m310 actions; the 32^3 x 96, L5 = 6
     # configuration keeps a15m310's (M5, b5, c5) rather than a09m310's (1.1, 1.25, 0.25)
     for l5, ens in ((12, 'a15m310'), (8, 'a12m310')):

@@ -19,7 +19,7 @@ import numpy as np
 import pytest
 
 import synth
-import sampled
+from oracle import sampled
 
 pytestmark = pytest.mark.gpu
 

@@ -419,7 +419,7 @@ def test_planted_mistakes():
 def test_sampled_site_operator_equals_full_operator():
     """The single-site D x used for sampled checks of full-size results equals the
     full-lattice D x at those sites (every boundary case of the window)."""
-    import sampled
+    from oracle import sampled
     dims, L5 = (4, 3, 2, 5), 4
     U = synth.random_gauge(dims, 21, 0.6)
     x = synth.gaussian_spinor((L5, 5, 2, 3, 4, 4, 3), 22)
