@@ -88,6 +88,8 @@ def parse():
                          '3 tensor-core (fp16), 4 autotuned including the staged and tensor-core forms, '
                          '6 CUDA-core direct, one unit per thread')
     ap.add_argument('--nsb', type=int, default=0, help='sites per thread block (0: chosen by the library)')
+    ap.add_argument('--link-recon', type=int, default=18, choices=[18, 12],
+                    help='reals per link read by the inner hops (12: third row rebuilt in the kernel)')
     ap.add_argument('--schur', default='asym', choices=['asym', 'sym'],
                     help='Schur form of the solve: asymmetric (default) or symmetric')
     ap.add_argument('--profile-steps', default='all', choices=['all', 'extra'],
@@ -354,9 +356,11 @@ def run_ours(args):
     dsrc = [torch.from_numpy(s).to('cuda') for s in srcs]
     dx = [torch.empty_like(s) for s in dsrc]
     schur = 1 if args.schur == 'sym' else 0
-    opts = M.mdwf_default_opts(precision=prec, profile=1, hop_variant=args.hop_variant, nsb=args.nsb, schur=schur)
+    opts = M.mdwf_default_opts(precision=prec, profile=1, hop_variant=args.hop_variant, nsb=args.nsb, schur=schur,
+                               link_recon=args.link_recon)
     opts_timed = opts if args.profile_steps == 'all' else M.mdwf_default_opts(
-        precision=prec, profile=0, hop_variant=args.hop_variant, nsb=args.nsb, schur=schur)
+        precision=prec, profile=0, hop_variant=args.hop_variant, nsb=args.nsb, schur=schur,
+        link_recon=args.link_recon)
 
     def barrier():
         if dist is not None:
@@ -409,10 +413,11 @@ def run_ours(args):
     # SURVEY 8(d) algorithmic bytes: input and output spinor (24 reals each) per unit, plus
     # 8 links of 18 reals per output site shared by its L5 x N units
     w, wg = REAL_BYTES[prec], LINK_REAL_BYTES[prec]
-    bytes_per_unit = 48 * w + 8 * 18 * wg / (L5 * n)
+    link_reals = args.link_recon if prec != 'double' else 18
+    bytes_per_unit = 48 * w + 8 * link_reals * wg / (L5 * n)
     bytes_per_launch = units * bytes_per_unit
     # what the launches store and load: + the fp16 scales, + `same` in half of the launches
-    stored_per_launch = units * 2.5 * BYTES_PER_UNIT[prec] + (V // 2) * 8 * 18 * wg
+    stored_per_launch = units * 2.5 * BYTES_PER_UNIT[prec] + (V // 2) * 8 * link_reals * wg
     achieved = bytes_per_launch / hop_avg_s / 1e9 if hop_avg_s else None
     peak, peak_kind = measured_peaks()
     gflops = units * 1320 / hop_avg_s / 1e9 if hop_avg_s else None
@@ -429,7 +434,8 @@ def run_ours(args):
     # end to end through the host-pointer C ABI call, pinned host buffers
     pin_src = [torch.from_numpy(s).pin_memory().numpy() for s in srcs]
     pin_x = [torch.empty(s.shape, dtype=torch.complex128).pin_memory().numpy() for s in srcs]
-    opts_e2e = M.mdwf_default_opts(precision=prec, hop_variant=args.hop_variant, nsb=args.nsb, schur=schur)
+    opts_e2e = M.mdwf_default_opts(precision=prec, hop_variant=args.hop_variant, nsb=args.nsb, schur=schur,
+                                   link_recon=args.link_recon)
     M.mdwf_solve_batch(ctx, 0, pin_src, W['tol'], masses=masses, opts=opts_e2e, out=pin_x)
     torch.cuda.synchronize()
     barrier()
@@ -518,7 +524,7 @@ def run_ours(args):
                        ' inner vectors; FP64 accumulator, reliable updates and sums',
             'data': 'synthetic',
             'config': dict(config_of(W, n, 'replicas' if world > 1 else 'single GPU'),
-                           schur=args.schur,
+                           schur=args.schur, link_reals=link_reals,
                            l2='inputs larger than L2: %.2f GB of inner vectors per step' % (
                                6 * units * BYTES_PER_UNIT[prec] / 1e9)),
             'latency_ms': {'p50': statistics.median(step_ms), 'p99': p99, 'per_step': step_ms},

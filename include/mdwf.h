@@ -91,6 +91,10 @@ typedef struct {
                             with a 16 times tighter Schur stopping norm, at most this often (default 3) */
   double stop_scale_test; /* testing only: multiplies the Schur stopping norm (default 1); above 1 the
                             first certificate misses tol, so the restarts above must finish the solve */
+  int link_recon;         /* reals read per link by the inner (FP32-arithmetic) hops: 18 (default) or 12,
+                            the first two rows, with the third rebuilt in the kernel as the conjugate
+                            cross product (SU(3); the antiperiodic time phase is a separate sign);
+                            applies to the default direct hop (hop_variant 0, 1) */
 } mdwf_solver_opts;
 
 typedef struct {
@@ -194,7 +198,8 @@ int mdwf_solve_batch_dev(mdwf_ctx* ctx, int cfg_id, int n, const double* const* 
  * kernels, tiling and storage precision (MDWF_PREC_*) as the CG iterations of
  * mdwf_solve_batch; odd sites of in_i are ignored and odd sites of out_i set
  * to zero.  hop_variant as in mdwf_solver_opts in its low 8 bits; bits 8..15, if
- * nonzero, fix the number of sites per thread block (a tuning knob).  Returns
+ * nonzero, fix the number of sites per thread block (a tuning knob); bit 16 reads
+ * 12-real links (opts.link_recon = 12).  Returns
  * after the work on `stream` has finished.
  * Errors: ARG, STATE, NOMEM, CUDA, TIMEOUT. */
 int mdwf_apply_schur_batch_dev(mdwf_ctx* ctx, int cfg_id, int n, const double* const* in, double* const* out,

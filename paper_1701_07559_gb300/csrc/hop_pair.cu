@@ -137,6 +137,29 @@ __device__ __forceinline__ void mul_recon(const float* l, const float2* h, float
   }
 }
 
+// Two-row (12-real) link: rows 0 and 1 are loaded (three 16-byte words), row 2
+// of an SU(3) matrix is the complex conjugate of their cross product,
+// W_2j = conj(W_0k W_1l - W_0l W_1k) for (j, k, l) cyclic; the time-boundary
+// phase is a separate sign, so every stored link has determinant 1.
+__device__ __forceinline__ void load_link12(const float* __restrict__ U12, long idx, float l[18]) {
+  const float4* p = reinterpret_cast<const float4*>(U12 + 12 * idx);
+  const float4 t0 = __ldg(p), t1 = __ldg(p + 1), t2 = __ldg(p + 2);
+  l[0] = t0.x; l[1] = t0.y; l[2] = t0.z; l[3] = t0.w;
+  l[4] = t1.x; l[5] = t1.y; l[6] = t1.z; l[7] = t1.w;
+  l[8] = t2.x; l[9] = t2.y; l[10] = t2.z; l[11] = t2.w;
+#pragma unroll
+  for (int j = 0; j < 3; j++) {
+    const int k = (j + 1) % 3, m = (j + 2) % 3;
+    const float akr = l[2 * k], aki = l[2 * k + 1], amr = l[2 * m], ami = l[2 * m + 1];
+    const float bkr = l[6 + 2 * k], bki = l[6 + 2 * k + 1], bmr = l[6 + 2 * m], bmi = l[6 + 2 * m + 1];
+    // c = a_k b_m - a_m b_k
+    const float cr = __fmaf_rn(akr, bmr, __fmaf_rn(-aki, bmi, __fmaf_rn(-amr, bkr, __fmul_rn(ami, bki))));
+    const float ci = __fmaf_rn(akr, bmi, __fmaf_rn(aki, bmr, __fmaf_rn(-amr, bki, -__fmul_rn(ami, bkr))));
+    l[12 + 2 * j] = cr;
+    l[12 + 2 * j + 1] = -ci;
+  }
+}
+
 // Thread coordinates of the (rt, J, nsb) block, J = ceil(L5 / 2).
 struct PThr {
   int r_l, j, site_l, row;   // row: the thread's row of the epilogue tile
@@ -164,7 +187,7 @@ __device__ __forceinline__ PThr pair_thread(const FastArgs<S, float>& a) {
   return t;
 }
 
-template <int MU, bool FWD, typename S>
+template <int MU, bool FWD, typename S, bool R12>
 __device__ __forceinline__ void pair_term(const FastArgs<S, float>& a, const Site& x, const PThr& t, float2* acc) {
   const float sg = (a.dagger ? 1.f : -1.f) * (FWD ? 1.f : -1.f);
   const int hn = nbr_half<MU, FWD>(a.g, x);
@@ -176,13 +199,11 @@ __device__ __forceinline__ void pair_term(const FastArgs<S, float>& a, const Sit
   if (bflip) f = neg2(f);
   const float2 fs = mul2(f, f2(sg));
   float l[18];
-  if (FWD) {
-    load_link<float>(a.U, ((long)a.out_par * a.g.Vh + t.h) * 4 + MU, l);
-    mul_recon<MU, false>(l, hh, f, fs, acc);
-  } else {
-    load_link<float>(a.U, ((long)(1 - a.out_par) * a.g.Vh + hn) * 4 + MU, l);
-    mul_recon<MU, true>(l, hh, f, fs, acc);
-  }
+  const long li = FWD ? ((long)a.out_par * a.g.Vh + t.h) * 4 + MU : ((long)(1 - a.out_par) * a.g.Vh + hn) * 4 + MU;
+  if (R12) load_link12(a.U12, li, l);
+  else load_link<float>(a.U, li, l);
+  if (FWD) mul_recon<MU, false>(l, hh, f, fs, acc);
+  else mul_recon<MU, true>(l, hh, f, fs, acc);
 }
 
 // ---------------------------------------------------------------------------
@@ -507,7 +528,8 @@ __device__ __forceinline__ void pair_epilogue(const FastArgs<S, float>& a, const
 #ifndef MDWF_PAIR_MAXREG
 #define MDWF_PAIR_MAXREG 128
 #endif
-template <typename S, int EPI>
+// R12: 12-real links (a.U12), the third row rebuilt; else the padded 18-real links (a.U).
+template <typename S, int EPI, bool R12>
 __global__ void __maxnreg__(MDWF_PAIR_MAXREG) hop_pair_kernel(FastArgs<S, float> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const PThr t = pair_thread<S>(a);
@@ -516,14 +538,14 @@ __global__ void __maxnreg__(MDWF_PAIR_MAXREG) hop_pair_kernel(FastArgs<S, float>
   for (int i = 0; i < 24; i++) acc[i] = f2(0.f);
   if (t.act && a.in != nullptr) {      // no input: a local fifth-dimension pass
     const Site x = make_site(a.g, a.out_par, t.h);
-    pair_term<0, true, S>(a, x, t, acc);
-    pair_term<0, false, S>(a, x, t, acc);
-    pair_term<1, true, S>(a, x, t, acc);
-    pair_term<1, false, S>(a, x, t, acc);
-    pair_term<2, true, S>(a, x, t, acc);
-    pair_term<2, false, S>(a, x, t, acc);
-    pair_term<3, true, S>(a, x, t, acc);
-    pair_term<3, false, S>(a, x, t, acc);
+    pair_term<0, true, S, R12>(a, x, t, acc);
+    pair_term<0, false, S, R12>(a, x, t, acc);
+    pair_term<1, true, S, R12>(a, x, t, acc);
+    pair_term<1, false, S, R12>(a, x, t, acc);
+    pair_term<2, true, S, R12>(a, x, t, acc);
+    pair_term<2, false, S, R12>(a, x, t, acc);
+    pair_term<3, true, S, R12>(a, x, t, acc);
+    pair_term<3, false, S, R12>(a, x, t, acc);
   }
   pair_epilogue<S, EPI>(a, t, acc, reinterpret_cast<float*>(smem_raw));
 }
@@ -552,12 +574,12 @@ template <typename S, int EPI>
 static cudaError_t launch_pair_one(const FastArgs<S, float>& a, const PairShape& p, cudaStream_t st) {
   const dim3 grid((unsigned)((a.g.Vh + p.nsb - 1) / p.nsb), (unsigned)((a.N + p.rt - 1) / p.rt));
   const dim3 block((unsigned)p.rt, (unsigned)p.J, (unsigned)p.nsb);
+  auto* kern = a.U12 != nullptr ? hop_pair_kernel<S, EPI, true> : hop_pair_kernel<S, EPI, false>;
   if (p.smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(hop_pair_kernel<S, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)p.smem);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
     if (e != cudaSuccess) return e;
   }
-  hop_pair_kernel<S, EPI><<<grid, block, p.smem, st>>>(a);
+  kern<<<grid, block, p.smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -578,6 +600,20 @@ cudaError_t launch_pair(const FastArgs<S, float>& a, int nsb, int epi, cudaStrea
     case E_AINVD_SAME: return launch_pair_one<S, E_AINVD_SAME>(a, p, st);
     default: return cudaErrorInvalidValue;
   }
+}
+
+__global__ void k_link12(const float* __restrict__ U32, float* __restrict__ U12, long nlinks) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nlinks * 3) return;
+  const long link = i / 3;
+  const int w = (int)(i - link * 3);
+  reinterpret_cast<float4*>(U12)[link * 3 + w] = __ldg(reinterpret_cast<const float4*>(U32 + kLinkStride32 * link) + w);
+}
+
+cudaError_t build_link12(const float* U32, float* U12, long nlinks, cudaStream_t st) {
+  const long n = nlinks * 3;
+  k_link12<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(U32, U12, nlinks);
+  return cudaGetLastError();
 }
 
 template cudaError_t launch_pair<float>(const FastArgs<float, float>&, int, int, cudaStream_t);

@@ -46,6 +46,7 @@ struct Cfg {
   double* U64 = nullptr;
   float* U32 = nullptr;
   uint32_t* F16 = nullptr;  // tensor-core hop: fp16 B fragments [parity][h][mu][fwd, bwd][32 lanes]
+  float* U12 = nullptr;     // two-row FP32 links for 12-real reconstruction (built on first use)
   Action act;
 };
 
@@ -446,6 +447,7 @@ struct FastOp {
   long long* launches = nullptr;
   const StageInfo* stage = nullptr;   // neighbour staging through shared memory, when the tiling allows
   const uint32_t* F16 = nullptr;      // fp16 link fragments for the tensor-core hop
+  const float* U12 = nullptr;         // two-row links: the paired hop reconstructs the third row
   bool mma = false;                   // use the tensor-core hop (fp16 storage only)
   bool mma_pipelined = false;         // its bulk-copy pipelined form
 
@@ -461,7 +463,8 @@ struct FastOp {
     FastArgs<S, T> a;
     a.g = g; a.L5 = L5; a.N = N; a.out_par = out_par; a.dagger = dagger; a.antiperiodic = anti;
     a.in = in.v; a.in_nrm = in.n; a.same = same.v; a.same_nrm = same.n; a.add = add.v; a.add_nrm = add.n;
-    a.out = out.v; a.out_nrm = out.n; a.U = U; a.F16 = F16; a.f = f; a.g_same = g_same; a.kappa = kappa;
+    a.out = out.v; a.out_nrm = out.n; a.U = U; a.F16 = F16; a.U12 = U12; a.f = f; a.g_same = g_same;
+    a.kappa = kappa;
     a.active = active;
     a.partials = partials;
     if (launches) *launches += 1;
@@ -710,6 +713,11 @@ struct BatchSolver {
     choose_hop(op32, cf, nsb, (variant == HOP_AUTO || variant == HOP_TUNE_ALL) ? HOP_DIRECT : variant, &stage);
     choose_hop(opS, cf, nsb, (variant == HOP_AUTO || variant == HOP_TUNE_ALL) ? HOP_DIRECT : variant, &stage);
     tune_request = (variant == HOP_AUTO || variant == HOP_TUNE_ALL) && nsb == 0 ? variant : -1;
+    // 12-real links (the third row reconstructed) for the inner hops; the FP32
+    // reliable updates keep the full links
+    opS.U12 = (!kFP64 && o.link_recon == 12) ? cf->U12 : nullptr;
+    if (!kFP64 && o.link_recon == 12 && cf->U12 == nullptr)
+      return fail(c, MDWF_ERR_STATE, "12-real links requested but not built");
     op64.launches = op32.launches = opS.launches = &launches;
     profiling = profile;
     F<double>* f64[] = {&x_acc, &x_hi, &x_o, &bhat, &rho64, &u64, &t64};
@@ -991,6 +999,16 @@ int check_cfg(mdwf_ctx* ctx, int cfg_id, Cfg** out) {
 
 cudaStream_t pick_stream(mdwf_ctx* ctx, void* s) { return s ? (cudaStream_t)s : ctx->stream; }
 
+// The two-row FP32 links of cfg for 12-real reconstruction, built on first use.
+int ensure_u12(mdwf_ctx* ctx, Cfg* cfg) {
+  if (cfg->U12) return MDWF_OK;
+  const long nlinks = ctx->g.V * 4;
+  CK(cudaMalloc(&cfg->U12, sizeof(float) * 12 * (size_t)nlinks));
+  CK(build_link12(cfg->U32, cfg->U12, nlinks, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return MDWF_OK;
+}
+
 // Device time of the phases of a solve (opts.profile): an event pair per phase
 // interval, read after the synchronisation that ends it.
 struct Phases {
@@ -1035,6 +1053,7 @@ int solve_batch_impl(mdwf_ctx* ctx, Cfg* cfg, int n, const double* const* srcs, 
   auto t0 = std::chrono::steady_clock::now();
   Phases ph;
   CK(ph.begin(o.profile != 0, st));
+  if (o.link_recon == 12) { if (int r12 = ensure_u12(ctx, cfg)) return r12; }
   BatchSolver<S> sv;
   int rc = sv.init(ctx, cfg, masses, o.nsb, o.profile != 0, o, st);
   if (rc != MDWF_OK) return rc;
@@ -1341,6 +1360,7 @@ struct SessionImpl : SessionBase {
     t0.resize(N);
     sv.wsp = prefix;
     sv.own_b = true;
+    if (o.link_recon == 12) { if (int r12 = ensure_u12(ctx, cf)) return r12; }
     int rc = sv.init(c, cf, masses, o.nsb, o.profile != 0, o, s);
     if (rc) return rc;
     sv.sc.delta2 = BatchSolver<S>::kFP64 ? 0.0 : o.delta * o.delta;
@@ -1708,6 +1728,10 @@ int schur_batch_impl(mdwf_ctx* ctx, Cfg* cfg, int n, const double* const* in, do
   si.extra_tx = 0;
   si.err = errw;
   choose_hop(op, cfg, (flags >> 8) & 0xff, flags & 0xff, &si);
+  if ((flags >> 16) & 1) {   // 12-real links (the paired hop reconstructs the third row)
+    if (int r12 = ensure_u12(ctx, cfg)) return r12;
+    op.U12 = std::is_same<T, double>::value ? nullptr : cfg->U12;
+  }
   Tiling tb = make_tiling(g.Vh, L5, N, 2, 1024);
   F<S> fin, fu, ft, fo;
   CK(ws_field<S>(ctx, "sb.in", units, &fin));
@@ -1785,6 +1809,7 @@ void mdwf_default_opts(mdwf_solver_opts* o) {
   o->hop_variant = 0;
   o->max_restarts = 3;
   o->stop_scale_test = 1.0;
+  o->link_recon = 18;
 }
 
 int mdwf_create(const int dims[4], int device, mdwf_ctx** out) {
@@ -1810,6 +1835,7 @@ int mdwf_destroy(mdwf_ctx* ctx) {
     if (kv.second.U64) cudaFree(kv.second.U64);
     if (kv.second.U32) cudaFree(kv.second.U32);
     if (kv.second.F16) cudaFree(kv.second.F16);
+    if (kv.second.U12) cudaFree(kv.second.U12);
   }
   for (auto& kv : ctx->ws)
     if (kv.second.first) cudaFree(kv.second.first);
@@ -1826,6 +1852,10 @@ int mdwf_load_gauge(mdwf_ctx* ctx, int cfg_id, const double* U, int t_antiperiod
   const Geom& g = ctx->g;
   const size_t n = (size_t)g.V * 4 * 18;
   if (!all_finite(U, n)) return fail(ctx, MDWF_ERR_NONFINITE, "gauge field has NaN/Inf");
+  {
+    auto it = ctx->cfgs.find(cfg_id);    // a two-row copy of a previous field is stale now
+    if (it != ctx->cfgs.end() && it->second.U12) { cudaFree(it->second.U12); it->second.U12 = nullptr; }
+  }
   // reorder to [parity][h][mu][18] (FP64) and [parity][h][mu][20] (FP32, padded)
   const size_t n32 = (size_t)g.V * 4 * kLinkStride32;
   std::vector<double> h64(n);

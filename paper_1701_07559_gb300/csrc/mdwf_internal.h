@@ -355,6 +355,7 @@ struct FastArgs {
   S* out; float* out_nrm;
   const T* U;
   const uint32_t* F16;  // tensor-core hop: fp16 B fragments [parity][h][mu][fwd, bwd][lane], or null
+  const float* U12 = nullptr;  // two-row (12-real) FP32 links [parity][h][mu][12] (hop_pair.cu only)
   Fifth<T> f;
   T g_same;             // coefficient of A same (E_A_SAME) / A^+ same (E_AD_SAME_BD)
   T kappa;              // coefficient of the hop term
@@ -392,6 +393,8 @@ int mma_max_threads();
 cudaError_t launch_fast_mma(const FastArgs<__half, float>& a, const Tiling& t, int epi, cudaStream_t st,
                             const StageInfo* stage, bool pipelined);
 cudaError_t build_link_frags(const double* U64, uint32_t* frag, long nlinks, cudaStream_t st);
+// Two-row copy of the padded FP32 links (hop_pair.cu): U12[link][0..11] = U32[link][0..11].
+cudaError_t build_link12(const float* U32, float* U12, long nlinks, cudaStream_t st);
 // Wilson flow (flow.cu): U in the C ABI gauge layout, Z: workspace of 3 * 4V * 18 doubles.
 cudaError_t wilson_flow(double* U, const int L[4], double eps, int nsteps, double* Z, cudaStream_t st);
 // Sum over sites of Re tr of the six plaquettes into *out (device); part: V doubles of workspace.

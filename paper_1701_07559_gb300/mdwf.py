@@ -46,7 +46,7 @@ class mdwf_solver_opts(ctypes.Structure):
                 ('chunk', ctypes.c_int), ('use_graph', ctypes.c_int), ('nsb', ctypes.c_int),
                 ('profile', ctypes.c_int), ('wait_timeout_s', ctypes.c_double), ('timeout_test', ctypes.c_int),
                 ('hop_variant', ctypes.c_int), ('schur', ctypes.c_int), ('max_restarts', ctypes.c_int),
-                ('stop_scale_test', ctypes.c_double)]
+                ('stop_scale_test', ctypes.c_double), ('link_recon', ctypes.c_int)]
 
 
 # the phases of mdwf_solve_stats.phase_ms

@@ -291,15 +291,16 @@ MASSES12 = [0.0022, 0.0102, 0.0126, 0.0158, 0.0216, 0.05, 0.1, 0.2, 0.3, 0.01, 0
 
 @pytest.mark.parametrize('precision,tol', [('double', 1e-13), ('single', 2e-6), ('half', 4e-3), ('bf16', 3e-2)])
 @pytest.mark.parametrize('dagger', [0, 1])
-@pytest.mark.parametrize('variant', [0, 1, 2, 3, 5, 6, 1 | (2 << 8), 6 | (2 << 8)])
+@pytest.mark.parametrize('variant', [0, 1, 2, 3, 5, 6, 1 | (2 << 8), 6 | (2 << 8), 1 | (1 << 16)])
 @pytest.mark.parametrize('L5,masses', [(5, [0.05, 0.01, 0.2, 0.0022, 0.1]),            # L5 N = 25
                                        (4, [0.05, 0.01, 0.2, 0.0022]),                 # L5 N = 16: tensor-core tiles
                                        (6, [0.05, 0.01, 0.2, 0.0022, 0.1, 0.3, 0.02, 0.07]),   # L5 N = 48
                                        (8, MASSES12), (12, MASSES12), (16, MASSES12)])
 def test_schur_batch_multi_rhs(precision, tol, dagger, variant, L5, masses):
     """The batched Schur operator (the solver's kernels, N RHS with different masses,
-    every hop variant; bits 8..15 of the variant fix the sites per block) against
-    the oracle, slot by slot, norm-wise and element by element."""
+    every hop variant; bits 8..15 of the variant fix the sites per block, bit 16
+    selects 12-real links) against the oracle, slot by slot, norm-wise and element
+    by element."""
     import torch
     dims = (6, 4, 4, 6)
     act = (1.2, 1.25, 0.25, 0.05)
@@ -346,6 +347,27 @@ def test_autotuner_choice_is_cached_and_keeps_results():
             _check_solution(L, b, x, s)
     finally:
         L.close()
+
+
+@pytest.mark.parametrize('precision', ['single', 'half', 'bf16'])
+def test_solve_with_12_real_links(precision):
+    """Inner hops on 12-real links (the third row rebuilt in the kernel) on a flowed
+    field with the antiperiodic time boundary: the solve is certified by the
+    oracle's D and equals the oracle's solution."""
+    dims, L5 = (4, 4, 4, 8), 6
+    act = (1.2, 1.25, 0.25, 0.05)
+    U = synth.flowed_gauge(dims, 7, 0.4, flow_t=0.2, flow_eps=0.02)
+    ctx = M.mdwf_create(dims, 0)
+    try:
+        M.mdwf_load_gauge(ctx, 0, U, 1)
+        M.mdwf_set_action(ctx, 0, *act, L5)
+        b = M.mdwf_make_source(ctx, 0, synth.point_source_4d(dims, 1, 2))
+        x, st = M.mdwf_solve(ctx, 0, b, 1e-10, M.mdwf_default_opts(precision=precision, link_recon=12))
+        assert st['converged'] and O.true_residual(U, b, x, *act) <= 1e-10
+        ref, _ = O.solve_schur(U, b, *act, tol=1e-13)
+        assert _rel(x, ref) < 1e-8
+    finally:
+        M.mdwf_destroy(ctx)
 
 
 @pytest.mark.parametrize('precision', ['double', 'half'])
