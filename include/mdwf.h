@@ -244,6 +244,38 @@ int mdwf_apply_dslash_dev(mdwf_ctx* ctx, int cfg_id, const double* in, double* o
                           void* stream);
 int mdwf_apply_mdwf_dev(mdwf_ctx* ctx, int cfg_id, const double* in, double* out, int dagger, void* stream);
 
+/* ---- Domain decomposition in time -----------------------------------------
+ * A lattice split along t into P sub-domains (multi-GPU mode of the paper's
+ * runs, Sec. VII, Table VII geometries 1.1.1.P): each sub-domain is a context
+ * of dims {Lx, Ly, Lz, Lt/P} (Lt/P even, so local and global parities agree)
+ * holding every L5 slice of its sites and the links of its slab.  A hop across
+ * the slab's time edges reads the neighbouring sub-domain's face, 12 reals per
+ * (3D site, slice): the next sub-domain's first slice projected as the forward
+ * hop projects it, and the previous sub-domain's last slice projected and
+ * multiplied by U_t^+ with the sender's own links, so no link crosses a
+ * boundary.  Faces are laid out [z][y][x][s][spin 2][colour 3][re, im]
+ * (Lx Ly Lz L5 12 doubles), device memory owned by the caller; the caller moves
+ * them between sub-domains (a device copy, or a send into the receiving GPU's
+ * own buffer).  FP64, one right-hand side, the API field layout (device).
+ *
+ * mdwf_dd_pack_faces_dev: the faces of the field the hop of `kind` reads
+ * (kind 0: in, for out = H in or H^+ in; kind 1: B in for D (dagger 0), in for
+ * D^+): face_prev gets the first slice (for the previous sub-domain),
+ * face_next the last slice (for the next one).  `dagger` as in the apply.
+ * mdwf_dd_apply_dev: out = H in, H^+ in (kind 0) or D in, D^+ in (kind 1) on
+ * the sub-domain, the time hops across its edges taken from halo_next (the
+ * next sub-domain's face_prev) and halo_prev (the previous one's face_next),
+ * each multiplied by its sign (-1 across the global antiperiodic time
+ * boundary, else 1; the context's own boundary flag is not used).  Both
+ * return after the work on `stream` has finished.  The result equals the
+ * undecomposed operator bit for bit (same operations in the same order).
+ * Errors: ARG (odd local time extent, bad kind, null pointer), STATE, CUDA. */
+int mdwf_dd_pack_faces_dev(mdwf_ctx* ctx, int cfg_id, int kind, int dagger, const double* in, double* face_prev,
+                           double* face_next, void* stream);
+int mdwf_dd_apply_dev(mdwf_ctx* ctx, int cfg_id, int kind, int dagger, const double* in, double* out,
+                      const double* halo_next, const double* halo_prev, double sign_next, double sign_prev,
+                      void* stream);
+
 /* ---- Solver sessions: continuous batching --------------------------------
  * A session keeps the device state of `slots` right-hand sides of one gauge
  * configuration resident.  Requests (a 5D source, a quark mass, an output field,

@@ -189,9 +189,36 @@ __device__ __forceinline__ void hop_term_at(const FastArgs<S, T>& a, int hn, boo
   reconstruct<MU, T>(chi, f, f * sg, acc);
 }
 
+// A time hop across an edge of a decomposed lattice, from the neighbouring
+// sub-domain's face (same operations and order as the local term: the sender
+// projected, and for the backward hop multiplied by U^+, exactly as hop_term_at).
+template <bool FWD, typename S, typename T>
+__device__ __forceinline__ void halo_term(const FastArgs<S, T>& a, const Site& x, long h, int s, int r, T* acc) {
+  const T sg = (a.dagger ? T(1) : T(-1)) * (FWD ? T(1) : T(-1));
+  const long lex3 = x.lex - (long)x.c[3] * x.stride[3];
+  const T* p = (FWD ? a.halo_fwd : a.halo_bwd) + ((lex3 * a.L5 + s) * a.N + r) * 12;
+  T hh[12], chi[12];
+#pragma unroll
+  for (int i = 0; i < 12; i++) hh[i] = p[i];
+  const T f = FWD ? a.halo_sgn_fwd : a.halo_sgn_bwd;
+  if (FWD) {
+    T l[18];
+    load_link<T>(a.U, ((long)a.out_par * a.g.Vh + h) * 4 + 3, l);
+    su3_mul<T, false>(l, hh, chi);
+    su3_mul<T, false>(l, hh + 6, chi + 6);
+    reconstruct<3, T>(chi, f, f * sg, acc);
+  } else {
+    reconstruct<3, T>(hh, f, f * sg, acc);
+  }
+}
+
 template <int MU, bool FWD, typename S, typename T>
 __device__ __forceinline__ void hop_term(const FastArgs<S, T>& a, const Site& x, long h, int s, int r, const S* sp,
                                          float snrm, T* acc) {
+  if (MU == 3 && a.halo_fwd != nullptr && (FWD ? x.c[3] == a.g.L[3] - 1 : x.c[3] == 0)) {
+    halo_term<FWD, S, T>(a, x, h, s, r, acc);
+    return;
+  }
   const bool bflip = MU == 3 && a.antiperiodic && (FWD ? x.c[3] == a.g.L[3] - 1 : x.c[3] == 0);
   hop_term_at<MU, FWD, S, T>(a, nbr_half<MU, FWD>(a.g, x), bflip, h, s, r, sp, snrm, acc);
 }
@@ -1396,6 +1423,48 @@ cudaError_t launch_fast_mma(const FastArgs<__half, float>& a, const Tiling& t, i
 cudaError_t build_link_frags(const double* U64, uint32_t* frag, long nlinks, cudaStream_t st) {
   const long n = nlinks * 64;
   k_link_frags<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(U64, frag, nlinks);
+  return cudaGetLastError();
+}
+
+// Faces of a time-split lattice: thread per unit of one parity field; the
+// projection and U^+ multiply are those of the receiving side's hop_term_at.
+__global__ void k_dd_pack(const double* __restrict__ in, Geom g, int par, int L5, int N, int dagger,
+                          const double* __restrict__ U, double* __restrict__ face_prev,
+                          double* __restrict__ face_next) {
+  const long u = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= g.Vh * L5 * N) return;
+  const long h = u / ((long)L5 * N);
+  const int rem = (int)(u - h * L5 * N);
+  const int s = rem / N, r = rem - s * N;
+  const Site x = make_site(g, par, h);
+  const bool first = x.c[3] == 0, last = x.c[3] == g.L[3] - 1;
+  if (!first && !last) return;
+  const long lex3 = x.lex - (long)x.c[3] * x.stride[3];
+  double psi[24], hh[12];
+  load24<double, double>(in, nullptr, u, psi);
+  const double dg = dagger ? 1.0 : -1.0;
+  if (first) {        // the previous sub-domain's forward term: sg = dg
+    project<3, double>(psi, dg, hh);
+    double* o = face_prev + ((lex3 * L5 + s) * N + r) * 12;
+#pragma unroll
+    for (int i = 0; i < 12; i++) o[i] = hh[i];
+  }
+  if (last) {         // the next sub-domain's backward term: sg = -dg, then U_t(x)^+
+    double l[18], chi[12];
+    project<3, double>(psi, -dg, hh);
+    load_link<double>(U, ((long)par * g.Vh + h) * 4 + 3, l);
+    su3_mul<double, true>(l, hh, chi);
+    su3_mul<double, true>(l, hh + 6, chi + 6);
+    double* o = face_next + ((lex3 * L5 + s) * N + r) * 12;
+#pragma unroll
+    for (int i = 0; i < 12; i++) o[i] = chi[i];
+  }
+}
+
+cudaError_t dd_pack_faces(const double* in, const Geom& g, int par, int L5, int N, int dagger, const double* U,
+                          double* face_prev, double* face_next, cudaStream_t st) {
+  const long n = g.Vh * L5 * N;
+  k_dd_pack<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(in, g, par, L5, N, dagger, U, face_prev, face_next);
   return cudaGetLastError();
 }
 

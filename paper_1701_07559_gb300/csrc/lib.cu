@@ -448,6 +448,9 @@ struct FastOp {
   const StageInfo* stage = nullptr;   // neighbour staging through shared memory, when the tiling allows
   const uint32_t* F16 = nullptr;      // fp16 link fragments for the tensor-core hop
   const float* U12 = nullptr;         // two-row links: the paired hop reconstructs the third row
+  const T* halo_fwd = nullptr;        // time-split domain decomposition: faces of the neighbours
+  const T* halo_bwd = nullptr;
+  T halo_sgn_fwd = T(1), halo_sgn_bwd = T(1);
   bool mma = false;                   // use the tensor-core hop (fp16 storage only)
   bool mma_pipelined = false;         // its bulk-copy pipelined form
 
@@ -465,6 +468,7 @@ struct FastOp {
     a.in = in.v; a.in_nrm = in.n; a.same = same.v; a.same_nrm = same.n; a.add = add.v; a.add_nrm = add.n;
     a.out = out.v; a.out_nrm = out.n; a.U = U; a.F16 = F16; a.U12 = U12; a.f = f; a.g_same = g_same;
     a.kappa = kappa;
+    a.halo_fwd = halo_fwd; a.halo_bwd = halo_bwd; a.halo_sgn_fwd = halo_sgn_fwd; a.halo_sgn_bwd = halo_sgn_bwd;
     a.active = active;
     a.partials = partials;
     if (launches) *launches += 1;
@@ -1659,6 +1663,70 @@ int apply_dev(mdwf_ctx* ctx, Cfg* cfg, int kind, int arg1, int arg2, const doubl
   return MDWF_OK;
 }
 
+// Time-split domain decomposition, FP64, one RHS: the operator of a local
+// sub-domain whose time neighbours across both edges come from faces.
+// kind 0: out = H in (dagger 0) or H^+ in; kind 1: out = D in or D^+ in.  With
+// pack set, the faces of the field the hop reads (in; B in for D) are written to
+// face_prev / face_next instead.  Faces: Lx Ly Lz * L5 * 12 doubles each.
+int dd_impl(mdwf_ctx* ctx, Cfg* cfg, bool pack, int kind, int dagger, const double* in_dev, double* out_dev,
+            double* face_prev, double* face_next, const double* halo_next, const double* halo_prev,
+            double sign_next, double sign_prev, cudaStream_t st) {
+  const Geom& g = ctx->g;
+  const int L5 = cfg->act.L5;
+  if (g.L[3] < 2 || (g.L[3] & 1)) return fail(ctx, MDWF_ERR_ARG, "dd: the local time extent must be even");
+  const long units = g.Vh * L5;
+  F<double> ie, io, te, to, oe, oo;
+  CK(ws_field<double>(ctx, "dd.ie", units, &ie));
+  CK(ws_field<double>(ctx, "dd.io", units, &io));
+  CK(ws_field<double>(ctx, "dd.te", units, &te));
+  CK(ws_field<double>(ctx, "dd.to", units, &to));
+  CK(pack_rhs<double>(in_dev, ie.v, nullptr, g, L5, 1, 0, 0, st));
+  CK(pack_rhs<double>(in_dev, io.v, nullptr, g, L5, 1, 1, 0, st));
+  cudaError_t me = cudaSuccess;
+  double* mass = (double*)ws_get(ctx, "dd.mass", sizeof(double), &me);
+  CK(me);
+  CK(cudaMemcpyAsync(mass, &cfg->act.mf, sizeof(double), cudaMemcpyHostToDevice, st));
+  FastOp<double, double> fo;
+  fo.g = g; fo.L5 = L5; fo.N = 1; fo.anti = cfg->anti; fo.U = cfg->U64; fo.st = st;
+  fo.f = make_fifth<double>(cfg->act, mass);
+  choose_hop(fo, cfg, 0, HOP_DIRECT, nullptr);
+  Tiling tb = make_tiling(g.Vh, L5, 1, 2, 512);
+  // the field the hop reads: B in for D, in otherwise
+  const bool bfirst = kind == 1 && !dagger;
+  if (bfirst) {
+    CK(bop<double>(ie.v, nullptr, te.v, nullptr, fo.f, tb, g.Vh, L5, 1, nullptr, st));
+    CK(bop<double>(io.v, nullptr, to.v, nullptr, fo.f, tb, g.Vh, L5, 1, nullptr, st));
+  }
+  const F<double> he = bfirst ? te : ie, ho = bfirst ? to : io;
+  if (pack) {
+    CK(dd_pack_faces(he.v, g, 0, L5, 1, dagger, cfg->U64, face_prev, face_next, st));
+    CK(dd_pack_faces(ho.v, g, 1, L5, 1, dagger, cfg->U64, face_prev, face_next, st));
+    CK(cudaStreamSynchronize(st));
+    return MDWF_OK;
+  }
+  CK(ws_field<double>(ctx, "dd.oe", units, &oe));
+  CK(ws_field<double>(ctx, "dd.oo", units, &oo));
+  fo.halo_fwd = halo_next;
+  fo.halo_bwd = halo_prev;
+  fo.halo_sgn_fwd = sign_next;
+  fo.halo_sgn_bwd = sign_prev;
+  F<double> none;
+  if (kind == 0) {
+    CK(fo.run(E_RAW, 0, dagger, ho, none, none, 0.0, 1.0, oe, nullptr, nullptr));
+    CK(fo.run(E_RAW, 1, dagger, he, none, none, 0.0, 1.0, oo, nullptr, nullptr));
+  } else if (!dagger) {   // D x = A x - 1/2 H B x
+    CK(fo.run(E_A_SAME, 0, 0, to, ie, none, 1.0, -0.5, oe, nullptr, nullptr));
+    CK(fo.run(E_A_SAME, 1, 0, te, io, none, 1.0, -0.5, oo, nullptr, nullptr));
+  } else {                // D^+ x = A^+ x - 1/2 B^+ H^+ x
+    CK(fo.run(E_AD_SAME_BD, 0, 1, io, ie, none, 1.0, -0.5, oe, nullptr, nullptr));
+    CK(fo.run(E_AD_SAME_BD, 1, 1, ie, io, none, 1.0, -0.5, oo, nullptr, nullptr));
+  }
+  CK(unpack_rhs<double>(oe.v, nullptr, out_dev, g, L5, 1, 0, 0, st));
+  CK(unpack_rhs<double>(oo.v, nullptr, out_dev, g, L5, 1, 1, 0, st));
+  CK(cudaStreamSynchronize(st));
+  return MDWF_OK;
+}
+
 template <typename S>
 int schur_apply_impl(mdwf_ctx* ctx, Cfg* cfg, const double* in_dev, double* out_dev, int dagger, cudaStream_t st) {
   using T = typename StoreTraits<S>::T;
@@ -2020,6 +2088,32 @@ int mdwf_apply_mdwf_dev(mdwf_ctx* ctx, int cfg_id, const double* in, double* out
   if (!in || !out) return fail(ctx, MDWF_ERR_ARG, "apply_mdwf_dev: null pointer");
   CK(cudaSetDevice(ctx->device));
   return apply_dev(ctx, cfg, 1, dagger ? 1 : 0, 0, in, out, pick_stream(ctx, stream));
+}
+
+int mdwf_dd_pack_faces_dev(mdwf_ctx* ctx, int cfg_id, int kind, int dagger, const double* in, double* face_prev,
+                           double* face_next, void* stream) {
+  Cfg* cfg;
+  int rc = check_cfg(ctx, cfg_id, &cfg);
+  if (rc) return rc;
+  if (!in || !face_prev || !face_next || (kind != 0 && kind != 1))
+    return fail(ctx, MDWF_ERR_ARG, "dd_pack_faces: bad kind or null pointer");
+  CK(cudaSetDevice(ctx->device));
+  return dd_impl(ctx, cfg, true, kind, dagger ? 1 : 0, in, nullptr, face_prev, face_next, nullptr, nullptr, 1.0, 1.0,
+                 pick_stream(ctx, stream));
+}
+
+int mdwf_dd_apply_dev(mdwf_ctx* ctx, int cfg_id, int kind, int dagger, const double* in, double* out,
+                      const double* halo_next, const double* halo_prev, double sign_next, double sign_prev,
+                      void* stream) {
+  Cfg* cfg;
+  int rc = check_cfg(ctx, cfg_id, &cfg);
+  if (rc) return rc;
+  if (!in || !out || !halo_next || !halo_prev || (kind != 0 && kind != 1))
+    return fail(ctx, MDWF_ERR_ARG, "dd_apply: bad kind or null pointer");
+  if (!std::isfinite(sign_next) || !std::isfinite(sign_prev)) return fail(ctx, MDWF_ERR_ARG, "dd_apply: bad sign");
+  CK(cudaSetDevice(ctx->device));
+  return dd_impl(ctx, cfg, false, kind, dagger ? 1 : 0, in, out, nullptr, nullptr, halo_next, halo_prev, sign_next,
+                 sign_prev, pick_stream(ctx, stream));
 }
 
 int mdwf_apply_schur_batch_dev(mdwf_ctx* ctx, int cfg_id, int n, const double* const* in, double* const* out,

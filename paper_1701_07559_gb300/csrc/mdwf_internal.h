@@ -356,6 +356,16 @@ struct FastArgs {
   const T* U;
   const uint32_t* F16;  // tensor-core hop: fp16 B fragments [parity][h][mu][fwd, bwd][lane], or null
   const float* U12 = nullptr;  // two-row (12-real) FP32 links [parity][h][mu][12] (hop_pair.cu only)
+  // Domain decomposition in time (hop_fast.cu kernels): when halo_fwd is set, the
+  // t-neighbours across both edges of the local lattice come from the faces of
+  // the neighbouring sub-domains instead of the local field: halo_fwd[(lex3 L5 + s) N + r]
+  // holds the 12 reals of the projected half spinor of the next sub-domain's
+  // first slice, halo_bwd those of U^+ times the projected half spinor of the
+  // previous sub-domain's last slice (lex3 = x + Lx (y + Ly z)); each face carries
+  // its boundary factor (-1 across the antiperiodic global time boundary).
+  const T* halo_fwd = nullptr;
+  const T* halo_bwd = nullptr;
+  T halo_sgn_fwd = T(1), halo_sgn_bwd = T(1);
   Fifth<T> f;
   T g_same;             // coefficient of A same (E_A_SAME) / A^+ same (E_AD_SAME_BD)
   T kappa;              // coefficient of the hop term
@@ -395,6 +405,12 @@ cudaError_t launch_fast_mma(const FastArgs<__half, float>& a, const Tiling& t, i
 cudaError_t build_link_frags(const double* U64, uint32_t* frag, long nlinks, cudaStream_t st);
 // Two-row copy of the padded FP32 links (hop_pair.cu): U12[link][0..11] = U32[link][0..11].
 cudaError_t build_link12(const float* U32, float* U12, long nlinks, cudaStream_t st);
+// Faces of one parity field for the time-split domain decomposition (hop_fast.cu):
+// sites at t = 0 give face_prev (the projected half spinor the previous
+// sub-domain's forward hop needs), sites at t = Lt - 1 give face_next (U_t^+ times
+// the projected half spinor its backward hop needs); layout as FastArgs::halo_*.
+cudaError_t dd_pack_faces(const double* in, const Geom& g, int par, int L5, int N, int dagger, const double* U,
+                          double* face_prev, double* face_next, cudaStream_t st);
 // Wilson flow (flow.cu): U in the C ABI gauge layout, Z: workspace of 3 * 4V * 18 doubles.
 cudaError_t wilson_flow(double* U, const int L[4], double eps, int nsteps, double* Z, cudaStream_t st);
 // Sum over sites of Re tr of the six plaquettes into *out (device); part: V doubles of workspace.

@@ -98,6 +98,8 @@ _sig = {
     'mdwf_apply_schur_batch_dev_noalloc': (_I, [_P, _I, _I, ctypes.POINTER(_P), ctypes.POINTER(_P), _P, _I, _I, _P]),
     'mdwf_apply_dslash_dev': (_I, [_P, _I, _P, _P, _I, _I, _P]),
     'mdwf_apply_mdwf_dev': (_I, [_P, _I, _P, _P, _I, _P]),
+    'mdwf_dd_pack_faces_dev': (_I, [_P, _I, _I, _I, _P, _P, _P, _P]),
+    'mdwf_dd_apply_dev': (_I, [_P, _I, _I, _I, _P, _P, _P, _P, _D, _D, _P]),
     'mdwf_extract_prop4d': (_I, [_P, ctypes.POINTER(_I), _I, _P]),
     'mdwf_session_bytes': (ctypes.c_longlong, [_P, _I, _I, _I]),
     'mdwf_session_create': (_I, [_P, _I, _I, ctypes.POINTER(mdwf_solver_opts), _D, _P, ctypes.POINTER(_P)]),
@@ -387,6 +389,33 @@ def mdwf_apply_mdwf_dev(ctx, cfg_id, psi, out, dagger=0, stream=None):
     sh = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
     _check(ctx, _lib.mdwf_apply_mdwf_dev(ctx.handle, int(cfg_id), _dev_ptr(psi, shape), _dev_ptr(out, shape),
                                          int(dagger), sh))
+
+
+def dd_face_shape(ctx, cfg_id):
+    """Shape of one time face of a sub-domain: (Lz, Ly, Lx, L5, 2 spins, 3 colours), complex."""
+    L5 = _shape5(ctx, cfg_id)[0]
+    Lx, Ly, Lz, _ = ctx.dims
+    return (Lz, Ly, Lx, L5, 2, 3)
+
+
+def mdwf_dd_pack_faces_dev(ctx, cfg_id, kind, dagger, psi, face_prev, face_next, stream=None):
+    """Faces of a time-split sub-domain (see include/mdwf.h); torch CUDA tensors."""
+    shape = _shape5(ctx, cfg_id)
+    fs = dd_face_shape(ctx, cfg_id)
+    sh = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+    _check(ctx, _lib.mdwf_dd_pack_faces_dev(ctx.handle, int(cfg_id), int(kind), int(dagger), _dev_ptr(psi, shape),
+                                            _dev_ptr(face_prev, fs), _dev_ptr(face_next, fs), sh))
+
+
+def mdwf_dd_apply_dev(ctx, cfg_id, kind, dagger, psi, out, halo_next, halo_prev, sign_next=1.0, sign_prev=1.0,
+                      stream=None):
+    """The operator of a time-split sub-domain with its halos (see include/mdwf.h)."""
+    shape = _shape5(ctx, cfg_id)
+    fs = dd_face_shape(ctx, cfg_id)
+    sh = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+    _check(ctx, _lib.mdwf_dd_apply_dev(ctx.handle, int(cfg_id), int(kind), int(dagger), _dev_ptr(psi, shape),
+                                       _dev_ptr(out, shape), _dev_ptr(halo_next, fs), _dev_ptr(halo_prev, fs),
+                                       float(sign_next), float(sign_prev), sh))
 
 
 def mdwf_extract_prop4d(x5d, dims, L5):
