@@ -82,11 +82,11 @@ def parse():
     ap.add_argument('--rhs', type=int, default=0, help='right-hand sides per step (0: the workload\'s)')
     ap.add_argument('--mode', default='solve', choices=['solve', 'op', 'serve'],
                     help="'op': only apply the batched Schur operator (the solver's hop kernels), for profiling")
-    ap.add_argument('--lattice', default=None, help="op mode: Lx,Ly,Lz,Lt instead of the workload's 16,16,16,48")
+    ap.add_argument('--lattice', default=None, help="Lx,Ly,Lz,Lt instead of the workload's (profiling captures)")
     ap.add_argument('--hop-variant', type=int, default=0,
                     help='0 autotuned (CUDA-core forms), 1 CUDA-core direct loads, 2 CUDA-core staged, '
                          '3 tensor-core (fp16), 4 autotuned including the staged and tensor-core forms, '
-                         '6 CUDA-core direct, one unit per thread')
+                         '6 CUDA-core direct, one unit per thread, 7 as 1 with prefetching (fp16)')
     ap.add_argument('--nsb', type=int, default=0, help='sites per thread block (0: chosen by the library)')
     ap.add_argument('--link-recon', type=int, default=18, choices=[18, 12],
                     help='reals per link read by the inner hops (12: third row rebuilt in the kernel)')
@@ -101,6 +101,10 @@ def parse():
                     help='serve mode: the resident configurations, Lx,Ly,Lz,Lt:L5 separated by ;')
     ap.add_argument('--slots', type=int, default=12, help='serve mode: maximum slots of one session')
     ap.add_argument('--hbm-budget-gb', type=float, default=0.0, help='serve mode: HBM budget (0: 85%% of free)')
+    ap.add_argument('--profile-region', action='store_true',
+                    help='bracket the timed solves with cudaProfilerStart/Stop (for ncu --profile-from-start off)')
+    ap.add_argument('--priorities', action='store_true',
+                    help='serve mode: rank the configurations\' streams by the cost of one request')
     return ap.parse_args()
 
 
@@ -219,6 +223,9 @@ def workload(args):
     W = dict(WORKLOADS[args.workload])
     W['key'] = args.workload
     W['precision'] = args.precision or W['precision']
+    if args.lattice:    # a smaller lattice of the same workload (profiling captures)
+        W['dims'] = tuple(int(v) for v in args.lattice.split(','))
+        W['name'] = W['name'] + ' (lattice %s)' % args.lattice
     n = args.rhs or W.get('rhs_default', len(W['masses']))
     W['masses'] = [W['masses'][k % len(W['masses'])] for k in range(n)]
     W['nsrc'] = n
@@ -268,6 +275,30 @@ def oracle_timing(W, U, n_iter, procs):
         out.update({'procs': procs, 'apply_wall_s_all': tp,
                     'solves_per_s_all': procs / (2.0 * tp * n_iter) if n_iter else None})
     return out
+
+
+def host_mem_available():
+    """MemAvailable of the host in bytes (None where /proc/meminfo is absent)."""
+    try:
+        with open('/proc/meminfo') as fh:
+            for line in fh:
+                if line.startswith('MemAvailable:'):
+                    return int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    return None
+
+
+def oracle_procs(W, n):
+    """Processes for the all-cores oracle leg: one per core, at most one per RHS
+    and 16, and at most as many as half the free host memory holds at about
+    twenty full 5D FP64 fields per process (the oracle's temporaries)."""
+    procs = min(host_cores(), n, 16)
+    avail = host_mem_available()
+    if avail:
+        per = 20 * W['L5'] * W['dims'][0] * W['dims'][1] * W['dims'][2] * W['dims'][3] * 12 * 16
+        procs = max(1, min(procs, int(0.5 * avail // per)))
+    return procs
 
 
 def host_cores():
@@ -378,6 +409,8 @@ def run_ours(args):
     clocks.start()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     stats = []
+    if args.profile_region:
+        torch.cuda.profiler.start()
     t0 = time.perf_counter()
     for i in range(args.steps):
         ev[i][0].record(stream)
@@ -387,6 +420,8 @@ def run_ours(args):
     barrier()
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
+    if args.profile_region:
+        torch.cuda.profiler.stop()
     clk = clocks.stop()
     timed = stats
     if args.profile_steps == 'extra':
@@ -430,6 +465,7 @@ def run_ours(args):
     variant = tuned['hop_variant'] if tuned else (args.hop_variant or 1)
     kernel_name = {1: 'hop_pair_kernel' if prec != 'double' else 'hop_fast_kernel_f64',
                    2: 'hop_staged_kernel', 3: 'hop_mma_kernel', 6: 'hop_fast_kernel'}.get(variant, 'hop_pair_kernel')
+    hop_form = 'prefetching' if (variant == 7 and prec == 'half' and args.link_recon == 18) else 'plain'
 
     # end to end through the host-pointer C ABI call, pinned host buffers
     pin_src = [torch.from_numpy(s).pin_memory().numpy() for s in srcs]
@@ -445,6 +481,7 @@ def run_ours(args):
         M.mdwf_solve_batch(ctx, 0, pin_src, W['tol'], masses=masses, opts=opts_e2e, out=pin_x)
         e2e_t.append(time.perf_counter() - t1)
     e2e_value = replicas.job_throughput(n * args.steps, sum(e2e_t), dist, 'cuda')
+    del pin_src, pin_x
     field_bytes = L5 * V * 24 * 8
 
     # plain FP64 single-RHS GPU CG on the first source, like for like: device
@@ -492,8 +529,7 @@ def run_ours(args):
                                                                               W['c5'], m0))}
             else:
                 n_iter = fp64['iters'] if fp64 else (iteration_record(W['key']) or {}).get('fp64_cgnr_iters')
-                procs = min(host_cores(), n, 16)
-                ot = oracle_timing(W, U, n_iter, procs)
+                ot = oracle_timing(W, U, n_iter, oracle_procs(W, n))
                 cpu = {'value': ot['solves_per_s_1core'], 'unit': 'solves/s', 'cores': 1, 'kind': 'oracle',
                        'sample': ('one FP64 oracle Schur-operator application on one RHS of this workload (%.1f s '
                                   'on one core); a CGNR iteration is two, a solve %s iterations (FP64 CGNR here)'
@@ -541,7 +577,7 @@ def run_ours(args):
             'fp64_gpu_cg': fp64,
             'speedup_vs_fp64_gpu_cg': (value / fp64['solves_per_s']) if fp64 else None,
             'autotuned': tuned,
-            'dslash': {'kernel': '%s<%s>' % (kernel_name, prec), 'launches_timed': hop_launches,
+            'dslash': {'kernel': '%s<%s>' % (kernel_name, prec), 'form': hop_form, 'launches_timed': hop_launches,
                        'avg_launch_us': hop_avg_s * 1e6 if hop_avg_s else None,
                        'GB_per_s': achieved, 'eff_GFLOP_per_s': gflops,
                        'units_per_launch': units, 'algorithmic_bytes_per_unit': bytes_per_unit,
@@ -587,7 +623,7 @@ def run_op(args):
     U = synth.flowed_gauge(W['dims'], W['seed'], W['eps'], W['flow_t'], W['flow_eps'])
     ctx = M.mdwf_create(W['dims'], 0)
     M.mdwf_load_gauge(ctx, 0, U, 1)
-    M.mdwf_set_action(ctx, 0, W['M5'], W['b5'], W['c5'], W['mf'], W['L5'])
+    M.mdwf_set_action(ctx, 0, W['M5'], W['b5'], W['c5'], W['masses'][0], W['L5'])
     Lx, Ly, Lz, Lt = W['dims']
     shape = (W['L5'], Lt, Lz, Ly, Lx, 4, 3)
     variant = args.hop_variant | (args.nsb << 8)
@@ -643,7 +679,8 @@ def run_serve(args):
     torch.cuda.set_device(0)
     args.precision = args.precision or 'half'
     budget = int(args.hbm_budget_gb * 1e9) if args.hbm_budget_gb > 0 else None
-    srv = serving.Server(device=0, hbm_budget=budget, tol=1e-10, precision=args.precision, max_slots=args.slots)
+    srv = serving.Server(device=0, hbm_budget=budget, tol=1e-10, precision=args.precision, max_slots=args.slots,
+                         priorities=args.priorities)
     names, dims = [], []
     t0 = time.perf_counter()
     for i, spec in enumerate(args.serve_lattices.split(';')):
@@ -687,7 +724,8 @@ def run_serve(args):
     queue_max = max(s[1] for s in srv.samples)
     srv.close()
     print(json.dumps({'mode': 'serve', 'metric': 'p50/p99 latency and solves/s of a Poisson stream of solves to 1e-10',
-                      'precision': args.precision, 'configs': names, 'masses': SERVE_MASSES,
+                      'precision': args.precision, 'priorities': args.priorities, 'configs': names,
+                      'masses': SERVE_MASSES, 'requests_per_rate': args.requests,
                       'sources': 'Z2 noise or point, 50/50', 'slots_max': args.slots,
                       'hbm_budget_bytes': srv.budget, 'hbm_peak_accounted_bytes': peak_bytes, 'queue_max': queue_max,
                       'capacity_solves_per_s': capacity, 'capacity_run': cap, 'runs': runs, 'setup_s': setup_s,

@@ -73,8 +73,9 @@ typedef struct {
   int timeout_test;      /* testing only: 1 makes each staged-copy wait expect bytes that never
                             arrive, so the bound above must end the call with MDWF_ERR_TIMEOUT */
   int hop_variant;       /* 0: automatic: the autotuner times the CUDA-core direct hop with 1..8
-                            sites per block once per (L5, N, precision) and context and keeps the
-                            fastest; all of them give identical results.
+                            sites per block (and, for fp16 storage, form 7 with 1..4) once per (L5, N,
+                            precision) and context and keeps the fastest; all of them give identical
+                            results.
                             1: CUDA-core hop with direct neighbour loads (FP32 arithmetic: two fifth-
                             dimension slices per thread in packed FP32); 2: CUDA-core hop with
                             neighbours staged in shared memory by bulk copies; 3: tensor-core colour
@@ -83,7 +84,10 @@ typedef struct {
                             4: as 0 with the staged and tensor-core hops among the candidates (their
                             roundings differ from the direct form); 5: tensor-core tiles double-buffered
                             through bulk copies (bounded waits); 6: CUDA-core direct hop, one
-                            (site, slice, RHS) unit per thread */
+                            (site, slice, RHS) unit per thread; 7: as 1, with the block's links in
+                            shared memory and each thread's neighbour loads issued two directions
+                            ahead by asynchronous copies (fp16 storage with 18-real links, else as 1;
+                            the same results as 1) */
   int schur;              /* 0: the asymmetric Schur operator A - D_eo A^-1 D_oe (default, the form
                             Chroma used, Sec. VII); 1: the symmetric form 1 - A^-1 D_eo A^-1 D_oe the
                             paper names as the next step (same x; CUDA-core hops only) */
@@ -94,7 +98,7 @@ typedef struct {
   int link_recon;         /* reals read per link by the inner (FP32-arithmetic) hops: 18 (default) or 12,
                             the first two rows, with the third rebuilt in the kernel as the conjugate
                             cross product (SU(3); the antiperiodic time phase is a separate sign);
-                            applies to the default direct hop (hop_variant 0, 1) */
+                            applies to the default direct hop (hop_variant 0, 1; 7 falls back to 1) */
 } mdwf_solver_opts;
 
 typedef struct {
@@ -223,16 +227,15 @@ int mdwf_apply_schur_batch_dev(mdwf_ctx* ctx, int cfg_id, int n, const double* c
  * masses must fit, e.g. FP64 up to about 87,000 (site, slice, RHS) units.  A
  * larger problem is rejected with MDWF_ERR_ARG and a message giving the size.
  *
- * The first call on a device looks up the array's device address (with that
- * device current) and caches it for the life of the process; make that first
- * call before any stream capture.  A device reset (cudaDeviceReset) makes the
- * cached address stale: do not use this entry point after one.  Every call
- * uses the same array, which keeps the previous call's
+ * The call is synchronous: it copies the masses from host memory and returns
+ * when its work on `stream` has finished, so it cannot be captured in a CUDA
+ * graph.  It looks up the array's device address on every call (no cached
+ * address survives a device reset).  Every call uses the same array, which
+ * keeps the previous call's
  * contents (the kernels overwrite what they read, and the one field that must
  * start at zero is cleared by the call itself); calls that overlap on the GPU --
  * from several streams or host threads at once -- race on the array and must be
- * serialised by the caller.  Returns when the work on `stream` has finished.
- * The paper has no counterpart to this entry point.
+ * serialised by the caller.  The paper has no counterpart to this entry point.
  * Errors: ARG (including a problem too large for the array), STATE, CUDA. */
 #define MDWF_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
 int mdwf_apply_schur_batch_dev_noalloc(mdwf_ctx* ctx, int cfg_id, int n, const double* const* in,
@@ -335,7 +338,9 @@ int mdwf_mres_correlators_dev(mdwf_ctx* ctx, int cfg_id, int n, double* const* x
  * solver uses for n right-hand sides of this configuration at `precision`
  * (include_tensor_core: also try the tensor-core hop), with its time for one
  * Mhat + Mhat^+ application.  Runs the timing once per (L5, n, precision,
- * candidate set) and context, then answers from the cache.  Outputs may be NULL.
+ * candidate set) and context, then answers from the cache.  The timing runs use
+ * (and leave allocated) the context's solver workspace for n RHS, the fields a
+ * solve of n RHS would use.  Outputs may be NULL.
  * Errors: ARG, STATE, NOMEM, CUDA, TIMEOUT. */
 int mdwf_autotune(mdwf_ctx* ctx, int cfg_id, int n, int precision, int include_tensor_core, int* hop_variant,
                   int* nsb, double* ms_per_pair);

@@ -5,6 +5,8 @@
 // sites x L5 slices x rt slots per block), so per-slot partial sums are formed
 // per tile in a fixed order and the final sum over tiles is also fixed: a
 // slot's result does not depend on how many other slots share the launch.
+#include <cooperative_groups.h>
+
 #include "blas.h"
 
 namespace mdwf {
@@ -94,7 +96,21 @@ __global__ void k_convert(const Si* __restrict__ in, const float* __restrict__ i
   store24<So, To>(out, out_nrm, x.u, b);
 }
 
-// x += alpha_r p ; rho -= alpha_r q ; partial |rho|^2
+// x += alpha_r p ; rho -= alpha_r q ; |rho|^2 of one unit, explicit roundings.
+__device__ __forceinline__ float axpy_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double axpy_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+template <typename TX, typename T>
+__device__ __forceinline__ T axpy_unit(T a, const T* pv, const T* qv, T* rv, TX* xv) {
+  T n2t = 0;
+#pragma unroll
+  for (int i = 0; i < 24; i++) {
+    xv[i] = axpy_fma((TX)a, (TX)pv[i], xv[i]);
+    rv[i] = axpy_fma(-a, qv[i], rv[i]);
+    n2t = axpy_fma(rv[i], rv[i], n2t);
+  }
+  return n2t;
+}
+
 template <typename SX, typename S>
 __global__ void k_axpy_x_rho(SX* __restrict__ xv, const S* __restrict__ p, const float* __restrict__ p_nrm,
                              S* __restrict__ rho, float* __restrict__ rho_nrm, const S* __restrict__ q,
@@ -112,14 +128,7 @@ __global__ void k_axpy_x_rho(SX* __restrict__ xv, const S* __restrict__ p, const
     load24<S, T>(q, q_nrm, x.u, qv);
     load24<S, T>(rho, rho_nrm, x.u, rv);
     load24<SX, TX>(xv, nullptr, x.u, xv_);
-    T n2t = 0;
-#pragma unroll
-    for (int i = 0; i < 24; i++) {
-      xv_[i] += (TX)(a * pv[i]);
-      rv[i] -= a * qv[i];
-      n2t += rv[i] * rv[i];
-    }
-    n2 = (double)n2t;
+    n2 = (double)axpy_unit<TX, T>(a, pv, qv, rv, xv_);
     store24<SX, TX>(xv, nullptr, x.u, xv_);
     store24<S, T>(rho, rho_nrm, x.u, rv);
   }
@@ -177,20 +186,38 @@ __global__ void k_norm2(const S* __restrict__ v, const float* __restrict__ v_nrm
   block_partial(n2, x, tl, L5, Vh, partials);
 }
 
-// out[r] = sum_h partials[r][h], fixed order: thread t takes sites t, t+T, ..., then a fixed tree.
-__global__ void k_finalize(const double* __restrict__ partials, long nsites, int N, double* __restrict__ out) {
+// out[r] = sum_h partials[r][h] in a fixed order that depends on nsites only: a
+// cluster of kFinCluster blocks per slot, block c summing the c-th contiguous
+// chunk (thread t takes sites t, t+256, ... of it, then a fixed tree), and block
+// 0 adding the blocks' sums in rank order through distributed shared memory.
+// Spreading a slot over several SMs matters on a part with few FP64 adders per SM.
+constexpr int kFinCluster = 8;
+__global__ void __cluster_dims__(kFinCluster, 1, 1) __launch_bounds__(256)
+    k_finalize(const double* __restrict__ partials, long nsites, double* __restrict__ out) {
+  namespace cg = cooperative_groups;
   __shared__ double sh[256];
-  const int r = blockIdx.x;
-  double s = 0.0;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int r = blockIdx.y;
+  const int c = (int)cluster.block_rank();
+  const long len = (nsites + kFinCluster - 1) / kFinCluster;
+  const long beg = (long)c * len;
+  const long end = beg + len < nsites ? beg + len : nsites;
   const double* p = partials + (long)r * nsites;
-  for (long k = threadIdx.x; k < nsites; k += blockDim.x) s += p[k];
+  double s = 0.0;
+  for (long k = beg + threadIdx.x; k < end; k += blockDim.x) s += p[k];
   sh[threadIdx.x] = s;
   __syncthreads();
   for (int w = blockDim.x / 2; w > 0; w >>= 1) {
     if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
     __syncthreads();
   }
-  if (threadIdx.x == 0) out[r] = sh[0];
+  cluster.sync();
+  if (c == 0 && threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int q = 0; q < kFinCluster; q++) tot += *cluster.map_shared_rank(&sh[0], q);
+    out[r] = tot;
+  }
+  cluster.sync();   // every block's sum stays readable until block 0 has added it
 }
 
 // u = B x on one parity: P_+ half b5 x_s + c5 x_{s-1}, P_- half b5 x_s + c5 x_{s+1},
@@ -531,7 +558,7 @@ cudaError_t mres_correlators(const double* const* xs, int n, long V, int Lt, int
 }
 
 cudaError_t finalize(const double* partials, long ntiles, int N, double* out, cudaStream_t st) {
-  k_finalize<<<N, 256, 0, st>>>(partials, ntiles, N, out);
+  k_finalize<<<dim3(kFinCluster, (unsigned)N), 256, 0, st>>>(partials, ntiles, out);
   return cudaGetLastError();
 }
 

@@ -1339,7 +1339,7 @@ template <typename S, typename T>
 cudaError_t launch_fast(const FastArgs<S, T>& a, const Tiling& t, int epi, cudaStream_t st, const StageInfo* stage) {
   if (stage && (t.rt != a.N || t.ngroups != 1 || a.in == nullptr)) stage = nullptr;
   if constexpr (std::is_same<T, float>::value) {
-    if (stage == nullptr && t.form == 0) return launch_pair<S>(a, t.nsb, epi, st);
+    if (stage == nullptr && (t.form == 0 || t.form == 2)) return launch_pair<S>(a, t.nsb, epi, st, t.form == 2);
   }
   switch (epi) {
     case E_SAME_AINV: return launch_one<S, T, E_SAME_AINV>(a, t, st, stage);

@@ -14,6 +14,15 @@
 // Every operation has an explicit rounding (fma.rn / mul.rn / add.rn, packed or
 // scalar), so a unit's result does not depend on the block shape or on which
 // lane of a pair it occupies: every tiling of this kernel gives the same bits.
+//
+// Prefetching form (fp16 storage, 18-real links): the block's eight links per
+// site are copied to shared memory once, and each thread streams its neighbour
+// pairs through a two-stage buffer of its own in shared memory with
+// asynchronous copies (cp.async), issuing the loads of direction k + 2 while it
+// computes direction k.  The arithmetic is the same, in the same order, so it
+// gives the same bits as the plain form.
+#include <type_traits>
+
 #include "mdwf_internal.h"
 #include "hop_common.cuh"
 
@@ -525,18 +534,175 @@ __device__ __forceinline__ void pair_epilogue(const FastArgs<S, float>& a, const
   }
 }
 
+// ---------------------------------------------------------------------------
+// Prefetching form: asynchronous copies into per-thread stages.
+// ---------------------------------------------------------------------------
+constexpr int kStageBytes = 112;   // two fp16 units (2 x 48 B) + their two scales, padded to 16 B
+constexpr int kLinkWords = 5;      // an FP32 link: five 16-byte words
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Term k of the hop: direction mu = k / 2, forward for even k.
+template <int K>
+__device__ __forceinline__ long pf_link_index(const FastArgs<__half, float>& a, const Site& x, long h) {
+  constexpr int MU = K / 2;
+  constexpr bool FWD = (K % 2) == 0;
+  if (FWD) return ((long)a.out_par * a.g.Vh + h) * 4 + MU;
+  return ((long)(1 - a.out_par) * a.g.Vh + nbr_half<MU, false>(a.g, x)) * 4 + MU;
+}
+
+// The block's links, [site_l][k][20 floats], loaded once by the whole block.
+__device__ __forceinline__ void pf_load_links(const FastArgs<__half, float>& a, float4* slink) {
+  const int nsb = blockDim.z;
+  const int nthr = blockDim.x * blockDim.y * blockDim.z;
+  const int tid = (threadIdx.z * blockDim.y + threadIdx.y) * blockDim.x + threadIdx.x;
+  for (int w = tid; w < nsb * 8 * kLinkWords; w += nthr) {
+    const int site_l = w / (8 * kLinkWords);
+    const int k = (w / kLinkWords) % 8;
+    const int word = w % kLinkWords;
+    const long h = (long)blockIdx.x * nsb + site_l;
+    if (h >= a.g.Vh) continue;
+    const Site x = make_site(a.g, a.out_par, h);
+    long li;
+    switch (k) {
+      case 0: li = pf_link_index<0>(a, x, h); break;
+      case 1: li = pf_link_index<1>(a, x, h); break;
+      case 2: li = pf_link_index<2>(a, x, h); break;
+      case 3: li = pf_link_index<3>(a, x, h); break;
+      case 4: li = pf_link_index<4>(a, x, h); break;
+      case 5: li = pf_link_index<5>(a, x, h); break;
+      case 6: li = pf_link_index<6>(a, x, h); break;
+      default: li = pf_link_index<7>(a, x, h); break;
+    }
+    slink[w] = __ldg(reinterpret_cast<const float4*>(a.U + kLinkStride32 * li) + word);
+  }
+}
+
+// Issue the copies of term K's two neighbour units and their scales into a stage.
+template <int K>
+__device__ __forceinline__ void pf_issue(const FastArgs<__half, float>& a, const Site& x, const PThr& t,
+                                         unsigned char* stage) {
+  constexpr int MU = K / 2;
+  constexpr bool FWD = (K % 2) == 0;
+  const int hn = nbr_half<MU, FWD>(a.g, x);
+  const long uA = ((long)hn * a.L5 + t.s0) * a.N + t.r;
+  const long uB = t.two ? uA + a.N : uA;
+  const uint4* pa = reinterpret_cast<const uint4*>(a.in + 24 * uA);
+  const uint4* pb = reinterpret_cast<const uint4*>(a.in + 24 * uB);
+  uint4* d = reinterpret_cast<uint4*>(stage);
+  cp_async16(d, pa);
+  cp_async16(d + 1, pa + 1);
+  cp_async16(d + 2, pa + 2);
+  cp_async16(d + 3, pb);
+  cp_async16(d + 4, pb + 1);
+  cp_async16(d + 5, pb + 2);
+  float* sc = reinterpret_cast<float*>(d + 6);
+  cp_async4(sc, a.in_nrm + uA);
+  cp_async4(sc + 1, a.in_nrm + uB);
+}
+
+// Term K from a filled stage and the block's links (the operations of pair_term).
+template <int K>
+__device__ __forceinline__ void pf_compute(const FastArgs<__half, float>& a, const Site& x, const PThr& t,
+                                           const unsigned char* stage, const float4* slink, float2* acc) {
+  constexpr int MU = K / 2;
+  constexpr bool FWD = (K % 2) == 0;
+  const float sg = (a.dagger ? 1.f : -1.f) * (FWD ? 1.f : -1.f);
+  const bool bflip = MU == 3 && a.antiperiodic && (FWD ? x.c[3] == a.g.L[3] - 1 : x.c[3] == 0);
+  const uint4* q = reinterpret_cast<const uint4*>(stage);
+  uint4 qa[3], qb[3];
+  qa[0] = q[0]; qa[1] = q[1]; qa[2] = q[2];
+  qb[0] = q[3]; qb[1] = q[4]; qb[2] = q[5];
+  const float2 sc = *reinterpret_cast<const float2*>(q + 6);
+  float ha[12], hb[12];
+  project_half<MU>(qa, sg, ha);
+  project_half<MU>(qb, sg, hb);
+  float2 hh[12];
+#pragma unroll
+  for (int i = 0; i < 12; i++) hh[i] = make_float2(ha[i], hb[i]);
+  float2 f = sc;
+  if (bflip) f = neg2(f);
+  const float2 fs = mul2(f, f2(sg));
+  const float4* lw = slink + (t.site_l * 8 + K) * kLinkWords;
+  const float4 t0 = lw[0], t1 = lw[1], t2 = lw[2], t3 = lw[3], t4 = lw[4];
+  const float l[18] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w, t2.x,
+                       t2.y, t2.z, t2.w, t3.x, t3.y, t3.z, t3.w, t4.x, t4.y};
+  if (FWD) mul_recon<MU, false>(l, hh, f, fs, acc);
+  else mul_recon<MU, true>(l, hh, f, fs, acc);
+}
+
+// Step K of the two-stage pipeline: wait for term K, compute it, refill its stage with term K + 2.
+template <int K>
+__device__ __forceinline__ void pf_step(const FastArgs<__half, float>& a, const Site& x, const PThr& t,
+                                        unsigned char* stages, const float4* slink, float2* acc) {
+  unsigned char* stage = stages + (K & 1) * kStageBytes;
+  if (K < 7) cp_async_wait<1>();
+  else cp_async_wait<0>();
+  pf_compute<K>(a, x, t, stage, slink, acc);
+  if (K + 2 < 8) {
+    pf_issue<(K + 2) & 7>(a, x, t, stage);
+    cp_async_commit();
+  }
+}
+
+// Bytes of the epilogue tile (or the reduction buffer) at the start of shared memory.
+__host__ __device__ __forceinline__ size_t pair_tile_bytes(int threads, int nsb, int L5, int rt) {
+  const size_t tile = (size_t)threads * kRS * sizeof(float);
+  const size_t red = (size_t)nsb * L5 * rt * sizeof(double);
+  const size_t b = tile > red ? tile : red;
+  return (b + 15) & ~(size_t)15;
+}
+// Shared memory of the prefetching form beyond the tile: links and two stages per thread.
+__host__ __device__ __forceinline__ size_t pair_pf_bytes(int threads, int nsb) {
+  return (size_t)nsb * 8 * kLinkWords * 16 + (size_t)threads * 2 * kStageBytes;
+}
+
 #ifndef MDWF_PAIR_MAXREG
 #define MDWF_PAIR_MAXREG 128
 #endif
 // R12: 12-real links (a.U12), the third row rebuilt; else the padded 18-real links (a.U).
-template <typename S, int EPI, bool R12>
+// PF: the prefetching form (fp16 storage and 18-real links only).
+template <typename S, int EPI, bool R12, bool PF>
 __global__ void __maxnreg__(MDWF_PAIR_MAXREG) hop_pair_kernel(FastArgs<S, float> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const PThr t = pair_thread<S>(a);
   float2 acc[24];
 #pragma unroll
   for (int i = 0; i < 24; i++) acc[i] = f2(0.f);
-  if (t.act && a.in != nullptr) {      // no input: a local fifth-dimension pass
+  if constexpr (PF) {
+    static_assert(std::is_same<S, __half>::value && !R12, "the prefetching form is for fp16 and 18-real links");
+    const int threads = blockDim.x * blockDim.y * blockDim.z;
+    float4* slink = reinterpret_cast<float4*>(smem_raw + pair_tile_bytes(threads, blockDim.z, a.L5, blockDim.x));
+    unsigned char* stages = reinterpret_cast<unsigned char*>(slink + blockDim.z * 8 * kLinkWords) +
+                            (size_t)t.row * 2 * kStageBytes;
+    if (a.in != nullptr) pf_load_links(a, slink);
+    __syncthreads();
+    if (t.act && a.in != nullptr) {
+      const Site x = make_site(a.g, a.out_par, t.h);
+      pf_issue<0>(a, x, t, stages);
+      cp_async_commit();
+      pf_issue<1>(a, x, t, stages + kStageBytes);
+      cp_async_commit();
+      pf_step<0>(a, x, t, stages, slink, acc);
+      pf_step<1>(a, x, t, stages, slink, acc);
+      pf_step<2>(a, x, t, stages, slink, acc);
+      pf_step<3>(a, x, t, stages, slink, acc);
+      pf_step<4>(a, x, t, stages, slink, acc);
+      pf_step<5>(a, x, t, stages, slink, acc);
+      pf_step<6>(a, x, t, stages, slink, acc);
+      pf_step<7>(a, x, t, stages, slink, acc);
+    }
+  } else if (t.act && a.in != nullptr) {      // no input: a local fifth-dimension pass
     const Site x = make_site(a.g, a.out_par, t.h);
     pair_term<0, true, S, R12>(a, x, t, acc);
     pair_term<0, false, S, R12>(a, x, t, acc);
@@ -564,40 +730,48 @@ PairShape pair_shape(int L5, int N, int nsb) {
   if (rt < 1) rt = 1;
   p.rt = N < rt ? N : rt;
   p.threads = p.rt * p.J * p.nsb;
-  const size_t tile = (size_t)p.threads * kRS * sizeof(float);
-  const size_t red = (size_t)p.nsb * L5 * p.rt * sizeof(double);
-  p.smem = tile > red ? tile : red;
+  p.smem = pair_tile_bytes(p.threads, p.nsb, L5, p.rt);
+  p.smem_pf = p.smem + pair_pf_bytes(p.threads, p.nsb);
   return p;
 }
 
+constexpr size_t kPairMaxSmem = 200 * 1024;
+
 template <typename S, int EPI>
-static cudaError_t launch_pair_one(const FastArgs<S, float>& a, const PairShape& p, cudaStream_t st) {
+static cudaError_t launch_pair_one(const FastArgs<S, float>& a, const PairShape& p, bool pf, cudaStream_t st) {
   const dim3 grid((unsigned)((a.g.Vh + p.nsb - 1) / p.nsb), (unsigned)((a.N + p.rt - 1) / p.rt));
   const dim3 block((unsigned)p.rt, (unsigned)p.J, (unsigned)p.nsb);
-  auto* kern = a.U12 != nullptr ? hop_pair_kernel<S, EPI, true> : hop_pair_kernel<S, EPI, false>;
-  if (p.smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+  auto* kern = a.U12 != nullptr ? hop_pair_kernel<S, EPI, true, false> : hop_pair_kernel<S, EPI, false, false>;
+  size_t smem = p.smem;
+  if constexpr (std::is_same<S, __half>::value) {
+    if (pf && a.U12 == nullptr && p.smem_pf <= kPairMaxSmem) {
+      kern = hop_pair_kernel<S, EPI, false, true>;
+      smem = p.smem_pf;
+    }
+  }
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  kern<<<grid, block, p.smem, st>>>(a);
+  kern<<<grid, block, smem, st>>>(a);
   return cudaGetLastError();
 }
 
 template <typename S>
-cudaError_t launch_pair(const FastArgs<S, float>& a, int nsb, int epi, cudaStream_t st) {
+cudaError_t launch_pair(const FastArgs<S, float>& a, int nsb, int epi, cudaStream_t st, bool prefetch) {
   if (a.N < 1 || a.L5 < 1 || a.g.Vh < 1) return cudaErrorInvalidValue;
   const PairShape p = pair_shape(a.L5, a.N, nsb);
-  if (p.smem > 200 * 1024) return cudaErrorInvalidValue;
+  if (p.smem > kPairMaxSmem) return cudaErrorInvalidValue;
   switch (epi) {
-    case E_RAW: return launch_pair_one<S, E_RAW>(a, p, st);
-    case E_BAINV: return launch_pair_one<S, E_BAINV>(a, p, st);
-    case E_AINVD_BD: return launch_pair_one<S, E_AINVD_BD>(a, p, st);
-    case E_A_SAME: return launch_pair_one<S, E_A_SAME>(a, p, st);
-    case E_AD_SAME_BD: return launch_pair_one<S, E_AD_SAME_BD>(a, p, st);
-    case E_AINV_SAME: return launch_pair_one<S, E_AINV_SAME>(a, p, st);
-    case E_SAME_AINV: return launch_pair_one<S, E_SAME_AINV>(a, p, st);
-    case E_SAME_BD: return launch_pair_one<S, E_SAME_BD>(a, p, st);
-    case E_AINVD_SAME: return launch_pair_one<S, E_AINVD_SAME>(a, p, st);
+    case E_RAW: return launch_pair_one<S, E_RAW>(a, p, prefetch, st);
+    case E_BAINV: return launch_pair_one<S, E_BAINV>(a, p, prefetch, st);
+    case E_AINVD_BD: return launch_pair_one<S, E_AINVD_BD>(a, p, prefetch, st);
+    case E_A_SAME: return launch_pair_one<S, E_A_SAME>(a, p, prefetch, st);
+    case E_AD_SAME_BD: return launch_pair_one<S, E_AD_SAME_BD>(a, p, prefetch, st);
+    case E_AINV_SAME: return launch_pair_one<S, E_AINV_SAME>(a, p, prefetch, st);
+    case E_SAME_AINV: return launch_pair_one<S, E_SAME_AINV>(a, p, prefetch, st);
+    case E_SAME_BD: return launch_pair_one<S, E_SAME_BD>(a, p, prefetch, st);
+    case E_AINVD_SAME: return launch_pair_one<S, E_AINVD_SAME>(a, p, prefetch, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -616,8 +790,8 @@ cudaError_t build_link12(const float* U32, float* U12, long nlinks, cudaStream_t
   return cudaGetLastError();
 }
 
-template cudaError_t launch_pair<float>(const FastArgs<float, float>&, int, int, cudaStream_t);
-template cudaError_t launch_pair<__half>(const FastArgs<__half, float>&, int, int, cudaStream_t);
-template cudaError_t launch_pair<__nv_bfloat16>(const FastArgs<__nv_bfloat16, float>&, int, int, cudaStream_t);
+template cudaError_t launch_pair<float>(const FastArgs<float, float>&, int, int, cudaStream_t, bool);
+template cudaError_t launch_pair<__half>(const FastArgs<__half, float>&, int, int, cudaStream_t, bool);
+template cudaError_t launch_pair<__nv_bfloat16>(const FastArgs<__nv_bfloat16, float>&, int, int, cudaStream_t, bool);
 
 }  // namespace mdwf

@@ -519,7 +519,7 @@ struct FastOp {
 // Hop kernel variants: 0 automatic, 1 CUDA-core direct loads (two slices per thread for FP32
 // arithmetic), 2 CUDA-core staged, 3 tensor-core (fp16), 6 CUDA-core direct, one unit per thread.
 enum { HOP_AUTO = 0, HOP_DIRECT = 1, HOP_STAGED = 2, HOP_MMA = 3, HOP_TUNE_ALL = 4, HOP_MMA_PIPE = 5,
-       HOP_UNIT = 6 };
+       HOP_UNIT = 6, HOP_PAIR_PF = 7 };
 
 template <typename S>
 Tiling fast_tiling(const Geom& g, int L5, int N, int nsb_req, bool* staged, bool allow_staging);
@@ -549,7 +549,7 @@ void choose_hop(FastOp<S, T>& op, const Cfg* cfg, int nsb_req, int variant, cons
     if (mma_hop_usable(op.tl, L5, N)) { op.mma = true; op.stage = stage; return; }
   }
   op.tl = fast_tiling<S>(g, L5, N, nsb_req, &staged, variant == HOP_STAGED);
-  op.tl.form = variant == HOP_UNIT ? 1 : 0;
+  op.tl.form = variant == HOP_UNIT ? 1 : variant == HOP_PAIR_PF ? 2 : 0;
   op.stage = staged ? stage : nullptr;
 }
 
@@ -777,7 +777,8 @@ struct BatchSolver {
   // forms and block shapes on this solver's own fields, keep the fastest, and
   // remember it in the context for (L5, N, precision, candidate set).  HOP_AUTO
   // tries only forms with the same arithmetic (the CUDA-core direct hop with
-  // 1..8 sites per block), so the choice never changes a result; HOP_TUNE_ALL
+  // 1..8 sites per block and, for fp16 storage, its prefetching form with 1..4),
+  // so the choice never changes a result; HOP_TUNE_ALL
   // adds the staged and tensor-core hops, whose roundings differ.
   int tune(int which, int* variant_out = nullptr, int* nsb_out = nullptr, double* ms_out = nullptr) {
     mdwf_ctx* ctx = this->ctx;
@@ -789,6 +790,10 @@ struct BatchSolver {
       std::vector<std::array<int, 2>> cand;
       for (int nsbc : {1, 2, 4, 8})
         if (nsbc * L5 <= 1024) cand.push_back({HOP_DIRECT, nsbc});
+      // fp16 storage: the prefetching form of the paired hop, the same bits
+      if (std::is_same<S, __half>::value)
+        for (int nsbc : {1, 2, 4})
+          if (nsbc * L5 <= 1024) cand.push_back({HOP_PAIR_PF, nsbc});
       if (which == HOP_TUNE_ALL && !kFP64) cand.push_back({HOP_STAGED, 0});
       if (which == HOP_TUNE_ALL && std::is_same<S, __half>::value) cand.push_back({HOP_MMA, 0});
       cudaStream_t st = op64.st;
@@ -805,7 +810,7 @@ struct BatchSolver {
         choose_hop(opS, cfg, cnd[1], cnd[0], &stage);
         if (cnd[0] == HOP_MMA && !opS.mma) continue;
         if (cnd[0] == HOP_STAGED && opS.stage == nullptr) continue;
-        if (cnd[0] == HOP_DIRECT && opS.tl.nsb != cnd[1]) continue;
+        if ((cnd[0] == HOP_DIRECT || cnd[0] == HOP_PAIR_PF) && opS.tl.nsb != cnd[1]) continue;
         float ms = 0.f;
         cudaError_t e = cudaSuccess;
         for (int rep = 0; rep < 3 && e == cudaSuccess; rep++) {
@@ -1225,6 +1230,7 @@ int solve_batch_impl(mdwf_ctx* ctx, Cfg* cfg, int n, const double* const* srcs, 
     CK(sv.norms(sv.rho64, nullptr, tmp));
     CK(cudaMemcpyAsync(re.data(), tmp, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(iters.data(), sv.sc.iters, sizeof(int) * N, cudaMemcpyDeviceToHost, st));
+    sv.launches += 2 * N;
     for (int i = 0; i < N; i++) {
       CK(unpack_rhs<double>(sv.x_acc.v, nullptr, xs[i], g, L5, N, 0, i, st));
       CK(unpack_rhs<double>(sv.x_o.v, nullptr, xs[i], g, L5, N, 1, i, st));
@@ -2257,8 +2263,9 @@ int mdwf_autotune(mdwf_ctx* ctx, int cfg_id, int n, int precision, int include_t
   o.precision = precision;
   o.hop_variant = include_tensor_core ? HOP_TUNE_ALL : HOP_AUTO;
   std::vector<double> m(n, cfg->act.mf);
+  // the timing runs use the solver workspace of the context (the fields a solve of
+  // n RHS uses and re-initialises), so they need no second set of fields
   auto run = [&](auto& sv) -> int {
-    sv.wsp = "autotune.";
     int r = sv.init(ctx, cfg, m, 0, false, o, ctx->stream);
     if (r) return r;
     return sv.tune(o.hop_variant, hop_variant, nsb, ms_per_pair);
@@ -2270,7 +2277,6 @@ int mdwf_autotune(mdwf_ctx* ctx, int cfg_id, int n, int precision, int include_t
     case MDWF_PREC_BF16: { BatchSolver<__nv_bfloat16> sv; rc = run(sv); break; }
     default: return fail(ctx, MDWF_ERR_ARG, "autotune: unknown precision");
   }
-  ws_release_prefix(ctx, "autotune.");
   return rc;
 }
 
@@ -2381,25 +2387,17 @@ namespace {
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[MDWF_NOALLOC_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mu;
-unsigned char* g_noalloc_addr[kMaxDevices] = {nullptr};   // device address of the array, per device
-
 // Device address of the scratch array on ctx's device (which must be current).
-// In host code the array's name is only a stand-in, so the address is looked up
-// once per device and cached.
+// In host code the array's name is only a stand-in; the address is looked up
+// on every call (a host-side lookup that allocates nothing), so it is never
+// stale after a context reset.
 int noalloc_scratch(mdwf_ctx* ctx, unsigned char** out) {
-  if (ctx->device < 0 || ctx->device >= kMaxDevices) return fail(ctx, MDWF_ERR_ARG, "device index out of range");
-  std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (g_noalloc_addr[ctx->device] == nullptr) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || p == nullptr)
-      return fail(ctx, MDWF_ERR_CUDA, std::string("cudaGetSymbolAddress of the scratch array: ") +
-                                          cudaGetErrorString(e));
-    g_noalloc_addr[ctx->device] = static_cast<unsigned char*>(p);
-  }
-  *out = g_noalloc_addr[ctx->device];
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || p == nullptr)
+    return fail(ctx, MDWF_ERR_CUDA, std::string("cudaGetSymbolAddress of the scratch array: ") +
+                                        cudaGetErrorString(e));
+  *out = static_cast<unsigned char*>(p);
   return MDWF_OK;
 }
 

@@ -292,7 +292,8 @@ struct Tiling {
   long ntiles; // ceil(Vh / nsb)
   int ngroups; // ceil(N / rt)
   int threads; // nsb * L5 * rt
-  int form = 0; // FP32-arithmetic direct hop: 0 two slices per thread (hop_pair.cu), 1 one unit per thread
+  int form = 0; // FP32-arithmetic direct hop: 0 two slices per thread (hop_pair.cu), 1 one unit per thread,
+                // 2 two slices per thread with prefetching (hop_pair.cu)
 };
 
 inline Tiling make_tiling(long Vh, int L5, int N, int nsb, int max_threads = 1024) {
@@ -389,11 +390,14 @@ cudaError_t launch_fast(const FastArgs<S, T>& a, const Tiling& t, int epi, cudaS
 // Two-slices-per-thread hop (hop_pair.cu): block (rt, J = ceil(L5 / 2), nsb).
 struct PairShape {
   int J, nsb, rt, threads;
-  size_t smem;
+  size_t smem;      // plain form: the epilogue tile (or the reduction buffer)
+  size_t smem_pf;   // prefetching form: + the block's links + two stages per thread
 };
 PairShape pair_shape(int L5, int N, int nsb);
+// prefetch: the prefetching form where it applies (fp16 storage, 18-real links,
+// shared memory within bounds), else the plain form; both give the same bits.
 template <typename S>
-cudaError_t launch_pair(const FastArgs<S, float>& a, int nsb, int epi, cudaStream_t st);
+cudaError_t launch_pair(const FastArgs<S, float>& a, int nsb, int epi, cudaStream_t st, bool prefetch);
 // Tensor-core hop (fp16 storage): usable when a block holds whole sites and L5 N % 8 == 0.
 bool mma_hop_usable(const Tiling& t, int L5, int N);
 int mma_max_threads();

@@ -326,7 +326,7 @@ def mdwf_solve_batch_dev(ctx, cfg_id, srcs, xs, tol, masses=None, opts=None, str
     return [s.as_dict() for s in st]
 
 
-HOP_AUTO, HOP_DIRECT, HOP_STAGED, HOP_MMA, HOP_TUNE_ALL, HOP_MMA_PIPE, HOP_UNIT = 0, 1, 2, 3, 4, 5, 6
+HOP_AUTO, HOP_DIRECT, HOP_STAGED, HOP_MMA, HOP_TUNE_ALL, HOP_MMA_PIPE, HOP_UNIT, HOP_PAIR_PF = 0, 1, 2, 3, 4, 5, 6, 7
 
 
 def mdwf_apply_schur_batch_dev(ctx, cfg_id, ins, outs, masses=None, dagger=0, precision=MDWF_PREC_HALF,

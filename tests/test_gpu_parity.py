@@ -291,7 +291,7 @@ MASSES12 = [0.0022, 0.0102, 0.0126, 0.0158, 0.0216, 0.05, 0.1, 0.2, 0.3, 0.01, 0
 
 @pytest.mark.parametrize('precision,tol', [('double', 1e-13), ('single', 2e-6), ('half', 4e-3), ('bf16', 3e-2)])
 @pytest.mark.parametrize('dagger', [0, 1])
-@pytest.mark.parametrize('variant', [0, 1, 2, 3, 5, 6, 1 | (2 << 8), 6 | (2 << 8), 1 | (1 << 16)])
+@pytest.mark.parametrize('variant', [0, 1, 2, 3, 5, 6, 7, 1 | (2 << 8), 6 | (2 << 8), 7 | (2 << 8), 1 | (1 << 16)])
 @pytest.mark.parametrize('L5,masses', [(5, [0.05, 0.01, 0.2, 0.0022, 0.1]),            # L5 N = 25
                                        (4, [0.05, 0.01, 0.2, 0.0022]),                 # L5 N = 16: tensor-core tiles
                                        (6, [0.05, 0.01, 0.2, 0.0022, 0.1, 0.3, 0.02, 0.07]),   # L5 N = 48
@@ -326,6 +326,44 @@ def test_schur_batch_multi_rhs(precision, tol, dagger, variant, L5, masses):
         M.mdwf_destroy(ctx)
 
 
+@pytest.mark.parametrize('dims,L5,n', [((6, 4, 4, 6), 12, 12), ((6, 4, 4, 6), 7, 5), ((4, 4, 2, 6), 3, 13),
+                                       ((4, 4, 2, 6), 12, 25), ((8, 6, 4, 10), 8, 12)])
+@pytest.mark.parametrize('nsb', [1, 2, 4])
+def test_prefetching_pair_hop_gives_the_same_bits(dims, L5, n, nsb):
+    """fp16: the prefetching form of the paired hop (links in shared memory, the
+    neighbour loads two directions ahead) against the plain form at the same block
+    shape, for odd L5 (a thread with one slice) and an RHS count that leaves a
+    partial block (25 RHS at L5 = 12 and four sites per block: 21 + 4): every
+    output bit is the same for Mhat and Mhat^+ (their four epilogues), and the
+    result matches the oracle element by element."""
+    import torch
+    act = (1.3, 1.5, 0.5, 0.05)
+    U = synth.random_gauge(dims, 23, 0.6)
+    ctx = M.mdwf_create(dims, 0)
+    try:
+        M.mdwf_load_gauge(ctx, 0, U, 1)
+        M.mdwf_set_action(ctx, 0, *act, L5)
+        shape = (L5,) + tuple(reversed(dims)) + (4, 3)
+        ev = O.parity_mask(dims)
+        masses = [0.01 * (k + 1) for k in range(n)]
+        xs = [O.restrict(synth.gaussian_spinor(shape, 300 + i), ev) for i in range(n)]
+        ins = [torch.from_numpy(x).cuda() for x in xs]
+        for dagger in (0, 1):
+            a = [torch.empty_like(t) for t in ins]
+            b = [torch.empty_like(t) for t in ins]
+            M.mdwf_apply_schur_batch_dev(ctx, 0, ins, a, masses=masses, dagger=dagger, precision='half',
+                                         hop_variant=M.HOP_DIRECT | (nsb << 8))
+            M.mdwf_apply_schur_batch_dev(ctx, 0, ins, b, masses=masses, dagger=dagger, precision='half',
+                                         hop_variant=M.HOP_PAIR_PF | (nsb << 8))
+            for x, y in zip(a, b):
+                assert torch.equal(x, y)
+            f = O.schur_op_dag if dagger else O.schur_op
+            k = n - 1
+            _check_elementwise(b[k].cpu().numpy(), f(U, xs[k], act[0], act[1], act[2], masses[k]), 'half')
+    finally:
+        M.mdwf_destroy(ctx)
+
+
 def test_autotuner_choice_is_cached_and_keeps_results():
     """The autotuner picks a hop form per (L5, N, precision); its default candidate
     set shares one arithmetic, so a solve gives the same bits with the tuned form
@@ -334,9 +372,9 @@ def test_autotuner_choice_is_cached_and_keeps_results():
     try:
         t1 = M.mdwf_autotune(L.ctx, 0, 3, 'half')
         t2 = M.mdwf_autotune(L.ctx, 0, 3, 'half')
-        assert t1 == t2 and t1['hop_variant'] in (M.HOP_DIRECT, M.HOP_STAGED) and t1['ms_per_pair'] > 0
+        assert t1 == t2 and t1['hop_variant'] in (M.HOP_DIRECT, M.HOP_PAIR_PF) and t1['ms_per_pair'] > 0
         ta = M.mdwf_autotune(L.ctx, 0, 3, 'half', include_tensor_core=True)
-        assert ta['hop_variant'] in (M.HOP_DIRECT, M.HOP_STAGED, M.HOP_MMA)
+        assert ta['hop_variant'] in (M.HOP_DIRECT, M.HOP_PAIR_PF, M.HOP_STAGED, M.HOP_MMA)
         bs = [synth.gaussian_spinor(L.shape, 40 + k) for k in range(3)]
         xa, sa = M.mdwf_solve_batch(L.ctx, 0, bs, 1e-10, opts=M.mdwf_default_opts(precision='half'))
         xd, sd = M.mdwf_solve_batch(L.ctx, 0, bs, 1e-10, opts=M.mdwf_default_opts(precision='half', hop_variant=1,
