@@ -270,6 +270,8 @@ def mdwf_solve_batch(ctx, cfg_id, srcs, tol, masses=None, opts=None, raise_on_no
     hs = [_host(s, shape) for s in srcs]
     if out is not None:
         xs = list(out)
+        if len(xs) != n:
+            raise ValueError('mdwf_solve_batch: %d sources but %d output arrays' % (n, len(xs)))
         for x in xs:
             if x.dtype != np.complex128 or x.shape != shape or not x.flags['C_CONTIGUOUS']:
                 raise ValueError('out arrays must be contiguous complex128 of shape %s' % (shape,))
@@ -311,11 +313,15 @@ def mdwf_solve_batch_dev(ctx, cfg_id, srcs, xs, tol, masses=None, opts=None, str
     """Batched solve on torch CUDA tensors (srcs read, xs written).  stream: torch.cuda.Stream or None."""
     shape = _shape5(ctx, cfg_id)
     n = len(srcs)
+    if len(xs) != n:
+        raise ValueError('mdwf_solve_batch_dev: %d sources but %d solutions' % (n, len(xs)))
     sp = (_P * n)(*[_dev_ptr(s, shape) for s in srcs])
     xp = (_P * n)(*[_dev_ptr(x, shape) for x in xs])
     m = None
     if masses is not None:
         m = np.ascontiguousarray(masses, dtype=np.float64)
+        if m.shape != (n,):
+            raise ValueError('mdwf_solve_batch_dev: masses must have one entry per source')
     st = (mdwf_solve_stats * n)()
     o = opts if opts is not None else mdwf_default_opts()
     sh = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
