@@ -54,7 +54,7 @@ WORKLOADS = {
     '48x64': dict(name='48^3x64 L5=8 a12m130-shaped light quark m_f=0.0022, flowed SU(3), spin-colour point '
                        'sources, tol 1e-10',
                   dims=(48, 48, 48, 64), L5=8, M5=1.2, b5=1.25, c5=0.25, masses=[0.0022] * 12, seed=4, eps=0.4,
-                  flow_t=1.0, flow_eps=0.01, sources='point12', tol=1e-10, precision='half', rhs_default=2),
+                  flow_t=1.0, flow_eps=0.01, sources='point12', tol=1e-10, precision='half', batch_default=4),
 }
 WORKLOAD = WORKLOADS['16x48']
 # algorithmic bytes of one stored real (input + output spinor, 24 reals each, and the
@@ -80,6 +80,8 @@ def parse():
                     help='4x8: the oracle-sized FP64 case; 16x48 (default, the headline line): a15m310; '
                          '24x64: a12m310, 24 RHS over two masses; 48x64: a12m130-shaped light quark')
     ap.add_argument('--rhs', type=int, default=0, help='right-hand sides per step (0: the workload\'s)')
+    ap.add_argument('--batch', type=int, default=0,
+                    help='right-hand sides per solve call (0: the workload\'s; all of a step where they fit in HBM)')
     ap.add_argument('--mode', default='solve', choices=['solve', 'op', 'serve'],
                     help="'op': only apply the batched Schur operator (the solver's hop kernels), for profiling")
     ap.add_argument('--lattice', default=None, help="Lx,Ly,Lz,Lt instead of the workload's (profiling captures)")
@@ -229,6 +231,7 @@ def workload(args):
     n = args.rhs or W.get('rhs_default', len(W['masses']))
     W['masses'] = [W['masses'][k % len(W['masses'])] for k in range(n)]
     W['nsrc'] = n
+    W['batch'] = min(n, args.batch or W.get('batch_default', n))
     W['lattice'] = '%d^3x%d' % (W['dims'][0], W['dims'][3]) if W['dims'][0] == W['dims'][1] == W['dims'][2] \
         else 'x'.join(str(d) for d in W['dims'])
     return W
@@ -380,12 +383,36 @@ def run_ours(args):
     ctx = M.mdwf_create(W['dims'], local)
     M.mdwf_load_gauge(ctx, 0, U, 1)
     M.mdwf_set_action(ctx, 0, W['M5'], W['b5'], W['c5'], W['masses'][0], W['L5'])
-    srcs = make_inputs(M, ctx, W)
-    n = len(srcs)
+    n = W['nsrc']
     masses = W['masses']
     stream = torch.cuda.current_stream()
-    dsrc = [torch.from_numpy(s).to('cuda') for s in srcs]
+    # the RHS of a step go through the solver in batches of W['batch'] (all at once
+    # where their FP64 source and solution fields fit in HBM next to the solver)
+    batch = W['batch']
+    chunks = [list(range(i, min(i + batch, n))) for i in range(0, n, batch)]
+    Lx, Ly, Lz, Lt = W['dims']
+    if len(chunks) == 1:
+        srcs = make_inputs(M, ctx, W)
+        dsrc = [torch.from_numpy(s).to('cuda') for s in srcs]
+        eta = None
+    else:
+        # batches share `batch` device source and solution fields; each batch's 5D
+        # sources are built on the device (mdwf_make_source_dev) from its 4D point
+        # sources, inside the step
+        srcs = None
+        dsrc = [torch.empty((W['L5'], Lt, Lz, Ly, Lx, 4, 3), dtype=torch.complex128, device='cuda')
+                for _ in range(batch)]
+        eta = torch.zeros((Lt, Lz, Ly, Lx, 4, 3), dtype=torch.complex128, device='cuda')
     dx = [torch.empty_like(s) for s in dsrc]
+
+    def load_chunk(c):
+        if eta is None:
+            return
+        for j, k in enumerate(c):
+            sp = (k % 12 if W['sources'] == 'point12' else 0)
+            eta.zero_()
+            eta[0, 0, 0, 0, sp // 3, sp % 3] = 1.0
+            M.mdwf_make_source_dev(ctx, 0, eta, dsrc[j], stream=stream)
     schur = 1 if args.schur == 'sym' else 0
     opts = M.mdwf_default_opts(precision=prec, profile=1, hop_variant=args.hop_variant, nsb=args.nsb, schur=schur,
                                link_recon=args.link_recon)
@@ -398,7 +425,13 @@ def run_ours(args):
             dist.barrier()
 
     def solve(o):
-        return M.mdwf_solve_batch_dev(ctx, 0, dsrc, dx, W['tol'], masses=masses, opts=o, stream=stream)
+        # per-RHS stats of the step, batch after batch (a list per batch)
+        out = []
+        for c in chunks:
+            load_chunk(c)
+            out.append(M.mdwf_solve_batch_dev(ctx, 0, dsrc[:len(c)], dx[:len(c)], W['tol'],
+                                              masses=[masses[k] for k in c], opts=o, stream=stream))
+        return out
 
     for _ in range(args.warmup):
         solve(opts)
@@ -434,22 +467,22 @@ def run_ours(args):
 
     # correctness of what was timed: every system of the last step reports its
     # FP64 full-lattice residual (the library's certificate)
-    last = timed[-1]
+    last = [s for ch in timed[-1] for s in ch]
     resid_max = max(s['rel_true_resid'] for s in last)
     assert all(s['converged'] for s in last), last
     iters = [s['iters'] for s in last]
 
     # dominant kernel: the inner-precision hop (4 launches per CG iteration)
-    hop_launches = sum(s[0]['hop_launches'] for s in stats)
-    hop_ms = sum(s[0]['hop_ms'] for s in stats)
-    units = last[0]['hop_units']
+    hop_launches = sum(ch[0]['hop_launches'] for st in stats for ch in st)
+    hop_ms = sum(ch[0]['hop_ms'] for st in stats for ch in st)
+    units = timed[-1][0][0]['hop_units']
     L5, V = W['L5'], W['dims'][0] * W['dims'][1] * W['dims'][2] * W['dims'][3]
     hop_avg_s = (hop_ms / hop_launches) / 1e3 if hop_launches else None
     # SURVEY 8(d) algorithmic bytes: input and output spinor (24 reals each) per unit, plus
     # 8 links of 18 reals per output site shared by its L5 x N units
     w, wg = REAL_BYTES[prec], LINK_REAL_BYTES[prec]
     link_reals = args.link_recon if prec != 'double' else 18
-    bytes_per_unit = 48 * w + 8 * link_reals * wg / (L5 * n)
+    bytes_per_unit = 48 * w + 8 * link_reals * wg / (L5 * len(chunks[0]))
     bytes_per_launch = units * bytes_per_unit
     # what the launches store and load: + the fp16 scales, + `same` in half of the launches
     stored_per_launch = units * 2.5 * BYTES_PER_UNIT[prec] + (V // 2) * 8 * link_reals * wg
@@ -459,37 +492,29 @@ def run_ours(args):
     # FP32 CUDA-core peak at the measured clock: 152 SMs x 128 lanes x 2 flops (FMA)
     mhz = clk.get('sm_mhz') or 2070.0
     fp32_peak_tflops = 152 * 128 * 2 * mhz * 1e6 / 1e12
-    gpu_launches = sum(s[0]['kernel_launches'] for s in timed)
-    tuned = M.mdwf_autotune(ctx, 0, n, prec, include_tensor_core=args.hop_variant == 4) \
+    gpu_launches = sum(ch[0]['kernel_launches'] for st in timed for ch in st)
+    tuned = M.mdwf_autotune(ctx, 0, len(chunks[0]), prec, include_tensor_core=args.hop_variant == 4) \
         if args.hop_variant in (0, 4) and args.nsb == 0 else None
     variant = tuned['hop_variant'] if tuned else (args.hop_variant or 1)
     kernel_name = {1: 'hop_pair_kernel' if prec != 'double' else 'hop_fast_kernel_f64',
                    2: 'hop_staged_kernel', 3: 'hop_mma_kernel', 6: 'hop_fast_kernel'}.get(variant, 'hop_pair_kernel')
     hop_form = 'prefetching' if (variant == 7 and prec == 'half' and args.link_recon == 18) else 'plain'
 
-    # end to end through the host-pointer C ABI call, pinned host buffers
-    pin_src = [torch.from_numpy(s).pin_memory().numpy() for s in srcs]
-    pin_x = [torch.empty(s.shape, dtype=torch.complex128).pin_memory().numpy() for s in srcs]
-    opts_e2e = M.mdwf_default_opts(precision=prec, hop_variant=args.hop_variant, nsb=args.nsb, schur=schur,
-                                   link_recon=args.link_recon)
-    M.mdwf_solve_batch(ctx, 0, pin_src, W['tol'], masses=masses, opts=opts_e2e, out=pin_x)
-    torch.cuda.synchronize()
-    barrier()
-    e2e_t = []
-    for _ in range(args.steps):
-        t1 = time.perf_counter()
-        M.mdwf_solve_batch(ctx, 0, pin_src, W['tol'], masses=masses, opts=opts_e2e, out=pin_x)
-        e2e_t.append(time.perf_counter() - t1)
-    e2e_value = replicas.job_throughput(n * args.steps, sum(e2e_t), dist, 'cuda')
-    del pin_src, pin_x
     field_bytes = L5 * V * 24 * 8
+    # the first solution of the last batch and its source, on the host, for the
+    # oracle's checks below (the device fields are freed before the end-to-end leg)
+    x0 = b0 = None
+    m0 = masses[chunks[-1][0]]
+    if rank == 0 and not args.no_cpu and world == 1:
+        x0 = dx[0].cpu().numpy()
+        b0 = srcs[chunks[-1][0]] if srcs is not None else dsrc[0].cpu().numpy()
 
-    # plain FP64 single-RHS GPU CG on the first source, like for like: device
+    # plain FP64 single-RHS GPU CG on the same input, like for like: device
     # pointers, one warm-up solve, CUDA events around each timed solve
     fp64 = None
     if not args.no_fp64:
         o64 = M.mdwf_default_opts(precision='double', hop_variant=1)
-        one = lambda: M.mdwf_solve_batch_dev(ctx, 0, dsrc[:1], dx[:1], W['tol'], masses=masses[:1], opts=o64,
+        one = lambda: M.mdwf_solve_batch_dev(ctx, 0, dsrc[:1], dx[:1], W['tol'], masses=[m0], opts=o64,
                                              stream=stream)
         one()
         k64 = max(1, min(args.steps, 2))
@@ -504,6 +529,39 @@ def run_ours(args):
                 'rel_true_resid': st64[0]['rel_true_resid'],
                 'precision': 'FP64 storage and arithmetic, 1 RHS, device pointers, warmed'}
 
+    # end to end through the host-pointer C ABI call, pinned host buffers.  Batched
+    # workloads: the first batch (at most as many RHS as 40 % of the free host
+    # memory holds twice), after the device fields are freed for the library's copies
+    e2e_idx = chunks[0]
+    if eta is None:
+        pin_src = [torch.from_numpy(s).pin_memory().numpy() for s in srcs]
+    else:
+        avail = host_mem_available()
+        if avail:
+            e2e_idx = e2e_idx[:max(1, min(len(e2e_idx), int(0.4 * avail // (2 * field_bytes))))]
+        load_chunk(e2e_idx)
+        pin_src = []
+        for j in range(len(e2e_idx)):
+            t = torch.empty(tuple(dsrc[j].shape), dtype=torch.complex128, pin_memory=True)
+            t.copy_(dsrc[j])
+            pin_src.append(t.numpy())
+        del dsrc, dx
+        torch.cuda.empty_cache()
+    pin_x = [torch.empty(s.shape, dtype=torch.complex128).pin_memory().numpy() for s in pin_src]
+    m_e2e = [masses[k] for k in e2e_idx]
+    opts_e2e = M.mdwf_default_opts(precision=prec, hop_variant=args.hop_variant, nsb=args.nsb, schur=schur,
+                                   link_recon=args.link_recon)
+    M.mdwf_solve_batch(ctx, 0, pin_src, W['tol'], masses=m_e2e, opts=opts_e2e, out=pin_x)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_t = []
+    for _ in range(args.steps):
+        t1 = time.perf_counter()
+        M.mdwf_solve_batch(ctx, 0, pin_src, W['tol'], masses=m_e2e, opts=opts_e2e, out=pin_x)
+        e2e_t.append(time.perf_counter() - t1)
+    e2e_value = replicas.job_throughput(len(e2e_idx) * args.steps, sum(e2e_t), dist, 'cuda')
+    del pin_src, pin_x
+
     out = None
     if rank == 0:
         cpu = None
@@ -513,9 +571,6 @@ def run_ours(args):
             # seconds (the 4^3 x 8 workload), else a bounded sample of applications
             from oracle import mdwf_oracle as O
             from oracle import sampled
-            x0 = dx[0].cpu().numpy()
-            b0 = srcs[0]
-            m0 = masses[0]
             if V <= 4096:
                 t1 = time.perf_counter()
                 xref, it_or = O.solve_schur(U, b0, W['M5'], W['b5'], W['c5'], m0, tol=W['tol'])
@@ -550,7 +605,7 @@ def run_ours(args):
                                         'is bounded by kappa x 1e-10'}
         lat = sorted(step_ms)
         p99 = lat[min(len(lat) - 1, int(np.ceil(0.99 * len(lat))) - 1)]
-        phases = {k: statistics.mean(s[0]['phase_ms'][k] for s in stats) for k in M.PHASES}
+        phases = {k: statistics.mean(sum(ch[0]['phase_ms'][k] for ch in st) for st in stats) for k in M.PHASES}
         out = {
             'metric': METRIC, 'value': value, 'unit': 'solves/s', 'n_gpus': world, 'steps': args.steps,
             'warmup': args.warmup, 'ms_per_step': total_s * 1e3 / args.steps, 'higher_is_better': True,
@@ -560,6 +615,7 @@ def run_ours(args):
                        ' inner vectors; FP64 accumulator, reliable updates and sums',
             'data': 'synthetic',
             'config': dict(config_of(W, n, 'replicas' if world > 1 else 'single GPU'),
+                           rhs_per_batch=len(chunks[0]), batches_per_step=len(chunks),
                            schur=args.schur, link_reals=link_reals,
                            l2='inputs larger than L2: %.2f GB of inner vectors per step' % (
                                6 * units * BYTES_PER_UNIT[prec] / 1e9)),
@@ -569,7 +625,7 @@ def run_ours(args):
             'reliable_updates': [s['reliable_updates'] for s in last],
             'fp32_updates': [s['fp32_updates'] for s in last],
             'fp64_rerefs': [s['fp64_rerefs'] for s in last],
-            'restarts': last[0]['restarts'],
+            'restarts': max(s['restarts'] for s in last),
             'phases_ms_per_step': phases,
             'hop_ms_per_step': hop_ms / len(stats),
             'profiled_steps': args.profile_steps,
@@ -593,8 +649,10 @@ def run_ours(args):
                              'peak_kind': 'derived: 152 SMs x 128 FP32 lanes x 2 flops x %.0f MHz' % mhz,
                              'flops_per_unit': 1320},
             'cpu_baseline': cpu,
-            'e2e': {'value': e2e_value, 'unit': 'solves/s', 'h2d_bytes_per_step': n * field_bytes,
-                    'd2h_bytes_per_step': n * field_bytes},
+            'e2e': dict({'value': e2e_value, 'unit': 'solves/s', 'h2d_bytes_per_step': len(e2e_idx) * field_bytes,
+                         'd2h_bytes_per_step': len(e2e_idx) * field_bytes},
+                        **({} if len(e2e_idx) == n else
+                           {'rhs_per_step': len(e2e_idx), 'note': 'one batch of the workload per host-pointer call'})),
             'gpu_launches': gpu_launches,
             'clocks': clk,
             'wall_s': wall,

@@ -31,6 +31,43 @@ __device__ __forceinline__ Unit unit_of(const Tiling& tl, long Vh, int L5, int N
   return x;
 }
 
+// The FP32 solution accumulator x_lo of the mixed-precision solver is stored
+// tile-major: block b = blockIdx.y * gridDim.x + blockIdx.x of the BLAS tiling
+// holds its T = tl.threads units as six planes of float4 (plane k: components
+// 4k .. 4k+3 of the [spin][colour][re, im] order), thread t's plane k at float4
+// index (6 b + k) T + t.  One plane of a warp is 512 contiguous bytes, where the
+// unit-major layout would stride each thread's 16 bytes by 96.  Every kernel that
+// touches x_lo uses the same tiling; the field holds xlo_units(tl) units.  An
+// FP64 accumulator (the FP64 solver) keeps the unit-major layout.
+template <typename SX>
+struct XloLayout {
+  static __device__ __forceinline__ void load(const SX* v, const Unit& x, const Tiling&, SX a[24]) {
+    load24<SX, SX>(v, nullptr, x.u, a);
+  }
+  static __device__ __forceinline__ void store(SX* v, const Unit& x, const Tiling&, const SX a[24]) {
+    store24<SX, SX>(v, nullptr, x.u, a);
+  }
+};
+template <>
+struct XloLayout<float> {
+  static __device__ __forceinline__ long base(const Tiling& tl) {
+    return ((long)blockIdx.y * gridDim.x + blockIdx.x) * 6 * tl.threads + threadIdx.x;
+  }
+  static __device__ __forceinline__ void load(const float* v, const Unit&, const Tiling& tl, float a[24]) {
+    const float4* p = reinterpret_cast<const float4*>(v) + base(tl);
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+      const float4 t = __ldg(p + (long)k * tl.threads);
+      a[4 * k] = t.x; a[4 * k + 1] = t.y; a[4 * k + 2] = t.z; a[4 * k + 3] = t.w;
+    }
+  }
+  static __device__ __forceinline__ void store(float* v, const Unit&, const Tiling& tl, const float a[24]) {
+    float4* p = reinterpret_cast<float4*>(v) + base(tl);
+#pragma unroll
+    for (int k = 0; k < 6; k++) p[(long)k * tl.threads] = make_float4(a[4 * k], a[4 * k + 1], a[4 * k + 2], a[4 * k + 3]);
+  }
+};
+
 // Per-site, per-slot sum of `v` over the L5 slices (fixed order), written to
 // partials[r][h]; the final sum over sites is then independent of the tiling.
 __device__ __forceinline__ void block_partial(double v, const Unit& x, const Tiling& tl, int L5, long Vh,
@@ -127,9 +164,9 @@ __global__ void k_axpy_x_rho(SX* __restrict__ xv, const S* __restrict__ p, const
     load24<S, T>(p, p_nrm, x.u, pv);
     load24<S, T>(q, q_nrm, x.u, qv);
     load24<S, T>(rho, rho_nrm, x.u, rv);
-    load24<SX, TX>(xv, nullptr, x.u, xv_);
+    XloLayout<SX>::load(xv, x, tl, xv_);
     n2 = (double)axpy_unit<TX, T>(a, pv, qv, rv, xv_);
-    store24<SX, TX>(xv, nullptr, x.u, xv_);
+    XloLayout<SX>::store(xv, x, tl, xv_);
     store24<S, T>(rho, rho_nrm, x.u, rv);
   }
   block_partial(n2, x, tl, L5, Vh, partials);
@@ -162,11 +199,22 @@ __global__ void k_accum_xhi(double* __restrict__ xhi, SX* __restrict__ xlo, Tili
   double h[24];
   TX l[24];
   load24<double, double>(xhi, nullptr, x.u, h);
-  load24<SX, TX>(xlo, nullptr, x.u, l);
+  XloLayout<SX>::load(xlo, x, tl, l);
 #pragma unroll
   for (int i = 0; i < 24; i++) { h[i] += (double)l[i]; l[i] = 0; }
   store24<double, double>(xhi, nullptr, x.u, h);
-  store24<SX, TX>(xlo, nullptr, x.u, l);
+  XloLayout<SX>::store(xlo, x, tl, l);
+}
+
+// x_lo = 0 for the slots in mask (x_lo in the accumulator layout)
+template <typename SX>
+__global__ void k_zero_xlo(SX* __restrict__ xlo, Tiling tl, long Vh, int L5, int N, const int* __restrict__ mask) {
+  Unit x = unit_of(tl, Vh, L5, N);
+  if (!x.valid || !mask[x.r]) return;
+  SX z[24];
+#pragma unroll
+  for (int i = 0; i < 24; i++) z[i] = 0;
+  XloLayout<SX>::store(xlo, x, tl, z);
 }
 
 template <typename S>
@@ -491,6 +539,16 @@ cudaError_t accum_xhi(double* xhi, SX* xlo, const Tiling& t, long Vh, int L5, in
   return cudaGetLastError();
 }
 
+template <typename SX>
+cudaError_t zero_xlo(SX* xlo, const Tiling& t, long Vh, int L5, int N, const int* mask, cudaStream_t st) {
+  k_zero_xlo<SX><<<tile_grid(t), t.threads, 0, st>>>(xlo, t, Vh, L5, N, mask);
+  return cudaGetLastError();
+}
+
+long xlo_units(const Tiling& t, long units, bool tile_major) {
+  return tile_major ? t.ntiles * (long)t.ngroups * t.threads : units;
+}
+
 template <typename S>
 cudaError_t norm2_partials(const S* v, const float* v_nrm, const Tiling& t, long Vh, int L5, int N, const int* mask,
                            double* partials, cudaStream_t st) {
@@ -614,5 +672,7 @@ MDWF_INST_AXPY(float, __nv_bfloat16)
 
 template cudaError_t accum_xhi<double>(double*, double*, const Tiling&, long, int, int, const int*, cudaStream_t);
 template cudaError_t accum_xhi<float>(double*, float*, const Tiling&, long, int, int, const int*, cudaStream_t);
+template cudaError_t zero_xlo<double>(double*, const Tiling&, long, int, int, const int*, cudaStream_t);
+template cudaError_t zero_xlo<float>(float*, const Tiling&, long, int, int, const int*, cudaStream_t);
 
 }  // namespace mdwf

@@ -28,6 +28,14 @@ cudaError_t xpay(const S* r, const float* r_nrm, S* p, float* p_nrm, const doubl
 template <typename SX>
 cudaError_t accum_xhi(double* xhi, SX* xlo, const Tiling& t, long Vh, int L5, int N, const int* mask,
                       cudaStream_t st);
+// x_lo = 0 for the slots in mask.
+template <typename SX>
+cudaError_t zero_xlo(SX* xlo, const Tiling& t, long Vh, int L5, int N, const int* mask, cudaStream_t st);
+// Units a solution accumulator x_lo holds for the tiling t: an FP32 accumulator
+// is stored tile-major (see blas.cu) and spans every thread of the grid; an
+// FP64 one is unit-major, `units` long.  axpy_x_rho, accum_xhi and zero_xlo read
+// and write x_lo in that layout, and must be given the same tiling.
+long xlo_units(const Tiling& t, long units, bool tile_major);
 
 template <typename S>
 cudaError_t norm2_partials(const S* v, const float* v_nrm, const Tiling& t, long Vh, int L5, int N, const int* mask,

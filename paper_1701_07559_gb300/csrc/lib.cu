@@ -649,11 +649,14 @@ struct BatchSolver {
   FastOp<float, float> op32;
   FastOp<S, T> opS;
   Tiling tl_blas;
-  // FP64: sources, solution (x_acc + x_hi on even sites, x_o), reference residual bhat
+  // FP64: sources, solution (x_acc + x_hi on even sites, x_o), reference residual bhat.
+  // The batch solve keeps no x_o of its own: its reconstruction writes the odd
+  // sites into x_hi, which is free by then (solve_batch_impl, finish).
   F<double> b_e, b_o, x_acc, x_hi, x_o, bhat, rho64, u64, t64;
   F<float> xf, uf, tf, qf;       // FP32 reliable updates
   F<S> p, u, t, q, rho, r;       // inner vectors
   F<SX> xlo;
+  long xlo_n = 0;                 // units x_lo holds (tile-major FP32: the whole BLAS grid)
   double* part = nullptr;
   double* mass64 = nullptr;
   float* mass32 = nullptr;
@@ -724,12 +727,15 @@ struct BatchSolver {
       return fail(c, MDWF_ERR_STATE, "12-real links requested but not built");
     op64.launches = op32.launches = opS.launches = &launches;
     profiling = profile;
-    F<double>* f64[] = {&x_acc, &x_hi, &x_o, &bhat, &rho64, &u64, &t64};
-    const char* n64[] = {"x_acc", "x_hi", "x_o", "bhat", "rho64", "u64", "t64"};
-    for (int i = 0; i < 7; i++) CK(ws_field<double>(c, wsp + n64[i], units, f64[i]));
+    F<double>* f64[] = {&x_acc, &x_hi, &bhat, &rho64, &u64, &t64};
+    const char* n64[] = {"x_acc", "x_hi", "bhat", "rho64", "u64", "t64"};
+    for (int i = 0; i < 6; i++) CK(ws_field<double>(c, wsp + n64[i], units, f64[i]));
     if (own_b) {
+      // sessions finish slots while others iterate: their sources and odd-site
+      // solutions need fields of their own
       CK(ws_field<double>(c, wsp + "b_e", units, &b_e));
       CK(ws_field<double>(c, wsp + "b_o", units, &b_o));
+      CK(ws_field<double>(c, wsp + "x_o", units, &x_o));
     }
     if (!kFP64) {
       // the FP32 reliable-update fields live in the FP64 temporaries u64 and t64:
@@ -744,7 +750,9 @@ struct BatchSolver {
     F<S>* fS[] = {&p, &u, &t, &q, &rho, &r};
     const char* nS[] = {"p", "u", "t", "q", "rho", "r"};
     for (int i = 0; i < 6; i++) CK(ws_field<S>(c, wsp + "S." + nS[i], units, fS[i]));
-    CK(ws_field<SX>(c, wsp + "xlo", units, &xlo));
+    // x_lo: tile-major over the BLAS tiling when it is FP32 (axpy_x_rho, accum_xhi, zero_xlo)
+    xlo_n = xlo_units(tl_blas, units, !kFP64);
+    CK(ws_field<SX>(c, wsp + "xlo", xlo_n, &xlo));
     part = (double*)ws_get(c, wsp + "partials", sizeof(double) * g.Vh * N, &e); CK(e);
     double* d = (double*)ws_get(c, wsp + "scal_d", sizeof(double) * 12 * N, &e); CK(e);
     int* ip = (int*)ws_get(c, wsp + "scal_i", sizeof(int) * 4 * N, &e); CK(e);
@@ -760,7 +768,7 @@ struct BatchSolver {
     const size_t b64 = sizeof(double) * 24 * (size_t)units;
     CK(cudaMemsetAsync(x_acc.v, 0, b64, st));
     CK(cudaMemsetAsync(x_hi.v, 0, b64, st));
-    CK(cudaMemsetAsync(xlo.v, 0, sizeof(SX) * 24 * (size_t)units, st));
+    CK(cudaMemsetAsync(xlo.v, 0, sizeof(SX) * 24 * (size_t)xlo_n, st));
     CK(cudaMemsetAsync(p.v, 0, sizeof(S) * 24 * (size_t)units, st));
     if (p.n) CK(cudaMemsetAsync(p.n, 0, sizeof(float) * (size_t)units, st));
     if (tune_request >= 0) {
@@ -1221,11 +1229,13 @@ int solve_batch_impl(mdwf_ctx* ctx, Cfg* cfg, int n, const double* const* srcs, 
     sv.launches += 2;
     CK(bop<double>(sv.x_acc.v, nullptr, sv.u64.v, nullptr, sv.op64.f, sv.tl_blas, g.Vh, L5, N, nullptr, st));
     CK(sv.op64.run(E_RAW, 1, 0, sv.u64, none, sv.b_o, 0.0, 0.5, sv.t64, nullptr, nullptr));
-    CK(sv.op64.run(E_AINV_SAME, 1, 0, none, sv.t64, none, 0.0, 0.0, sv.x_o, nullptr, nullptr));
-    CK(sv.op64.run(E_A_SAME, 1, 0, none, sv.x_o, sv.t64, -1.0, 0.0, sv.rho64, nullptr, nullptr));
+    // y = t64 now holds b_o: the odd-site solution goes into x_hi (b_o's field)
+    F<double> x_o = sv.x_hi;
+    CK(sv.op64.run(E_AINV_SAME, 1, 0, none, sv.t64, none, 0.0, 0.0, x_o, nullptr, nullptr));
+    CK(sv.op64.run(E_A_SAME, 1, 0, none, x_o, sv.t64, -1.0, 0.0, sv.rho64, nullptr, nullptr));
     CK(sv.norms(sv.rho64, nullptr, tmp));
     CK(cudaMemcpyAsync(ro.data(), tmp, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
-    CK(bop<double>(sv.x_o.v, nullptr, sv.u64.v, nullptr, sv.op64.f, sv.tl_blas, g.Vh, L5, N, nullptr, st));
+    CK(bop<double>(x_o.v, nullptr, sv.u64.v, nullptr, sv.op64.f, sv.tl_blas, g.Vh, L5, N, nullptr, st));
     CK(sv.op64.run(E_A_SAME, 0, 0, sv.u64, sv.x_acc, sv.b_e, -1.0, 0.5, sv.rho64, nullptr, nullptr));
     CK(sv.norms(sv.rho64, nullptr, tmp));
     CK(cudaMemcpyAsync(re.data(), tmp, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
@@ -1233,7 +1243,7 @@ int solve_batch_impl(mdwf_ctx* ctx, Cfg* cfg, int n, const double* const* srcs, 
     sv.launches += 2 * N;
     for (int i = 0; i < N; i++) {
       CK(unpack_rhs<double>(sv.x_acc.v, nullptr, xs[i], g, L5, N, 0, i, st));
-      CK(unpack_rhs<double>(sv.x_o.v, nullptr, xs[i], g, L5, N, 1, i, st));
+      CK(unpack_rhs<double>(x_o.v, nullptr, xs[i], g, L5, N, 1, i, st));
     }
     CK(cudaStreamSynchronize(st));
     CK(ph.mark(PH_FINAL, st));
@@ -1419,7 +1429,7 @@ struct SessionImpl : SessionBase {
     const int* m = sv.umask_d;
     CK(zero_masked<double>(sv.x_acc.v, nullptr, sv.tl_blas, g.Vh, L5, N, m, st));
     CK(zero_masked<double>(sv.x_hi.v, nullptr, sv.tl_blas, g.Vh, L5, N, m, st));
-    CK(zero_masked<typename BatchSolver<S>::SX>(sv.xlo.v, nullptr, sv.tl_blas, g.Vh, L5, N, m, st));
+    CK(zero_xlo<typename BatchSolver<S>::SX>(sv.xlo.v, sv.tl_blas, g.Vh, L5, N, m, st));
     CK(zero_masked<S>(sv.p.v, sv.p.n, sv.tl_blas, g.Vh, L5, N, m, st));
     CK(pack_rhs<double>(src, sv.b_e.v, nullptr, g, L5, N, 0, r, st));
     CK(pack_rhs<double>(src, sv.b_o.v, nullptr, g, L5, N, 1, r, st));
