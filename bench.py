@@ -54,7 +54,7 @@ WORKLOADS = {
     '48x64': dict(name='48^3x64 L5=8 a12m130-shaped light quark m_f=0.0022, flowed SU(3), spin-colour point '
                        'sources, tol 1e-10',
                   dims=(48, 48, 48, 64), L5=8, M5=1.2, b5=1.25, c5=0.25, masses=[0.0022] * 12, seed=4, eps=0.4,
-                  flow_t=1.0, flow_eps=0.01, sources='point12', tol=1e-10, precision='half', batch_default=4),
+                  flow_t=1.0, flow_eps=0.01, sources='point12', tol=1e-10, precision='half', batch_default=3),
 }
 WORKLOAD = WORKLOADS['16x48']
 # algorithmic bytes of one stored real (input + output spinor, 24 reals each, and the
