@@ -14,7 +14,7 @@ one batch) and '48x64' (a12m130-shaped light quark).
 
 Prints one JSON line (rank 0): solves/s, time to solution, iterations, updates,
 the FP64 certificate and the oracle's check of a solution, the per-phase device
-time, the dominant hop kernel against the HBM roofline (SURVEY 8(d) bytes) and
+time, the dominant hop kernel against the HBM roofline (algorithmic bytes) and
 the FP32 roofline, the FP64 single-RHS GPU CG on the same input, the oracle on
 the host cores (one core and all cores), and the same metric end to end through
 the host-pointer call.  ``--impl reference`` times the FP64 CPU oracle on a
@@ -57,7 +57,7 @@ WORKLOADS = {
                   flow_t=1.0, flow_eps=0.01, sources='point12', tol=1e-10, precision='half', batch_default=3),
 }
 WORKLOAD = WORKLOADS['16x48']
-# algorithmic bytes of one stored real (SURVEY 8(d): input + output spinor, 24 reals each, and the
+# algorithmic bytes of one stored real (input + output spinor, 24 reals each, and the
 # link share 8 links x 18 reals of each output site over its L5 x N units; FP32 links here)
 REAL_BYTES = {'half': 2, 'single': 4, 'bf16': 2, 'double': 8}
 LINK_REAL_BYTES = {'half': 4, 'single': 4, 'bf16': 4, 'double': 8}
@@ -478,7 +478,7 @@ def run_ours(args):
     units = timed[-1][0][0]['hop_units']
     L5, V = W['L5'], W['dims'][0] * W['dims'][1] * W['dims'][2] * W['dims'][3]
     hop_avg_s = (hop_ms / hop_launches) / 1e3 if hop_launches else None
-    # SURVEY 8(d) algorithmic bytes: input and output spinor (24 reals each) per unit, plus
+    # algorithmic bytes: input and output spinor (24 reals each) per unit, plus
     # 8 links of 18 reals per output site shared by its L5 x N units
     w, wg = REAL_BYTES[prec], LINK_REAL_BYTES[prec]
     link_reals = args.link_recon if prec != 'double' else 18
