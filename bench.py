@@ -337,7 +337,7 @@ def run_reference(args):
     line = {'impl': 'reference', 'metric': METRIC, 'value': value, 'unit': 'solves/s', 'n_gpus': args.gpus,
             'steps': len(times), 'warmup': args.warmup, 'ms_per_step': 1e3 * statistics.mean(times),
             'higher_is_better': True, 'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f64', 'data': 'synthetic',
-            'config': config_of(W, W['nsrc'], 'single host core'),
+            'config': config_of(W, W['nsrc'], 'single process'),
             'cpu_baseline': {'value': value, 'unit': 'solves/s', 'cores': 1, 'kind': 'oracle', 'sample': sample},
             'e2e': {'value': value, 'unit': 'solves/s', 'h2d_bytes_per_step': 0, 'd2h_bytes_per_step': 0}}
     print(json.dumps(line), flush=True)
@@ -355,11 +355,21 @@ def iteration_record(key='16x48'):
 
 
 def config_of(W, n, parallelism):
+    """The workload as both arms name it (the same keys and values at one process)."""
+    Lx, Ly, Lz, Lt = W['dims']
+    units = (Lx * Ly * Lz * Lt // 2) * W['L5'] * W.get('batch', n)
     return {'workload': W['name'], 'lattice': W['lattice'], 'L5': W['L5'], 'rhs_per_step': n,
             'action': {'M5': W['M5'], 'b5': W['b5'], 'c5': W['c5'], 'masses': sorted(set(W['masses']))},
             'gauge': 'exp(i %.1f H)%s' % (W['eps'], ', Wilson flow t=%g (RK3, eps %g, FP64)' % (
                 W['flow_t'], W['flow_eps']) if W['flow_t'] > 0 else ', no flow'),
-            'precision': W['precision'], 'parallelism': parallelism}
+            'precision': W['precision'], 'parallelism': parallelism,
+            'l2': l2_note(6 * units * BYTES_PER_UNIT[W['precision']])}
+
+
+def l2_note(nbytes):
+    if nbytes > 129e6:
+        return 'inputs larger than L2: %.2f GB of inner vectors per batch' % (nbytes / 1e9)
+    return 'inputs fit in L2: %.2f MB of inner vectors per batch, no flush between steps' % (nbytes / 1e6)
 
 
 # ---------------------------------------------------------------------------
@@ -614,11 +624,9 @@ def run_ours(args):
                         'bf16': 'bf16', 'double': 'fp64'}[prec] +
                        ' inner vectors; FP64 accumulator, reliable updates and sums',
             'data': 'synthetic',
-            'config': dict(config_of(W, n, 'replicas' if world > 1 else 'single GPU'),
-                           rhs_per_batch=len(chunks[0]), batches_per_step=len(chunks),
-                           schur=args.schur, link_reals=link_reals,
-                           l2='inputs larger than L2: %.2f GB of inner vectors per step' % (
-                               6 * units * BYTES_PER_UNIT[prec] / 1e9)),
+            'config': config_of(W, n, 'replicas' if world > 1 else 'single process'),
+            'solver': {'rhs_per_batch': len(chunks[0]), 'batches_per_step': len(chunks), 'schur': args.schur,
+                       'link_reals': link_reals, 'device': 'one GPU per process'},
             'latency_ms': {'p50': statistics.median(step_ms), 'p99': p99, 'per_step': step_ms},
             'time_to_solution_s': {'p50': statistics.median(step_ms) / 1e3, 'p99': p99 / 1e3},
             'iters': iters, 'rel_true_resid_max': resid_max,
