@@ -344,6 +344,19 @@ def run_reference(args):
     return 0
 
 
+def cgnr_flops_per_unit_iteration(L5):
+    """Algorithmic flops of one CGNR iteration on the asymmetric Schur operator per
+    (half-lattice site, slice, RHS) unit: four Wilson hops of 1320, two A^-1 of
+    48 L5, four B and two A of 72, and about 240 in the vector updates."""
+    return 4 * 1320 + 2 * 48 * L5 + 6 * 72 + 240
+
+
+def solver_tflops(vh, L5, iters, seconds):
+    """Sustained solver TFLOP/s of a step: the algorithmic flops of every RHS's
+    own iterations (vh * L5 units each) over the step's device time."""
+    return cgnr_flops_per_unit_iteration(L5) * vh * L5 * sum(iters) / seconds / 1e12
+
+
 def iteration_record(key='16x48'):
     """FP64 CGNR iteration count of the workload (profiles/workload_iterations.json,
     written from bench lines), used to scale oracle timing samples to solves/s."""
@@ -630,6 +643,7 @@ def run_ours(args):
             'latency_ms': {'p50': statistics.median(step_ms), 'p99': p99, 'per_step': step_ms},
             'time_to_solution_s': {'p50': statistics.median(step_ms) / 1e3, 'p99': p99 / 1e3},
             'iters': iters, 'rel_true_resid_max': resid_max,
+            'solver_tflops': solver_tflops(V // 2, L5, iters, total_s / args.steps),
             'reliable_updates': [s['reliable_updates'] for s in last],
             'fp32_updates': [s['fp32_updates'] for s in last],
             'fp64_rerefs': [s['fp64_rerefs'] for s in last],

@@ -48,3 +48,11 @@ def test_batch_option_overrides_the_workload_default():
     assert W['batch'] == 2 and W['nsrc'] == 12
     W = _workload('16x48', rhs=5)
     assert W['batch'] == 5 and W['masses'] == [0.0158] * 5
+
+
+def test_solver_flop_count():
+    # 4 hops x 1320 + 2 A^-1 x 48 L5 + 6 x 72 (B, A) + 240 (vector updates)
+    assert bench.cgnr_flops_per_unit_iteration(12) == 5280 + 1152 + 432 + 240
+    # one iteration of one RHS on 16^3 x 48 (98,304 half-lattice sites), L5 = 12, in one second
+    t = bench.solver_tflops(98304, 12, [1], 1.0)
+    assert abs(t - 7104 * 98304 * 12 / 1e12) < 1e-15
